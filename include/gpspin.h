@@ -1,0 +1,129 @@
+/*
+ * gpspin.h -- C ABI of the GB300 split-step Crank-Nicolson solver for the 2D
+ * rotating spin-1 Gross-Pitaevskii equation with Rashba or Dresselhaus
+ * spin-orbit (SO) coupling and Rabi coupling (arXiv 2105.10517, Supplementary
+ * Material, Eqs. S.1-S.6; solution method: split-step Crank-Nicolson in
+ * imaginary or real time, program summary "Solution method").
+ *
+ * Conventions shared by every call
+ *  - Plain C types only.  Host pointers are owned by the caller; device memory
+ *    is owned by the handle and released by gp_destroy.
+ *  - Wave functions are laid out psi[c][j][i] as interleaved (re, im) pairs,
+ *    c = 0, 1, 2 for the components m_F = +1, 0, -1, j the y index (ny rows),
+ *    i the x index (fastest).  Host buffers are always complex128
+ *    (2 * 3 * nx * ny doubles), whatever the storage precision on the device.
+ *  - Grid: cell centred, x_i = -xlen/2 + (i + 1/2) dx with dx = xlen / nx (same
+ *    for y); psi vanishes outside the box (zero Dirichlet data).
+ *  - Every call returns a gp_status (GP_OK = 0); a failing call leaves the
+ *    handle usable unless it returns GP_ERR_CUDA.  Calls are synchronous with
+ *    respect to the handle's stream: they return after the device work they
+ *    enqueued has finished.  A handle must not be used from two threads at once.
+ */
+#ifndef GPSPIN_H
+#define GPSPIN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GP_OK = 0,
+    GP_ERR_ARG = 1,       /* invalid argument or parameter set (nothing was changed)      */
+    GP_ERR_OOM = 2,       /* device allocation failed                                     */
+    GP_ERR_CUDA = 3,      /* a CUDA runtime call failed; the handle should be destroyed   */
+    GP_ERR_NONFINITE = 4, /* a reduction met NaN/Inf in psi; the state is kept as is      */
+    GP_ERR_UNSUPPORTED = 5/* parameters outside what the tabulated solver supports        */
+} gp_status;
+
+typedef enum { GP_IMAG = 0, GP_REAL = 1 } gp_mode;
+typedef enum { GP_SO_NONE = 0, GP_SO_RASHBA = 1, GP_SO_DRESSELHAUS = 2 } gp_so_type;
+typedef enum { GP_FP64 = 0 } gp_precision;
+
+/* Problem statement (Eqs. S.1-S.4 and the input parameters of the program
+ * summary): grid nx x ny on [-xlen/2, xlen/2) x [-ylen/2, ylen/2), time step dt,
+ * trap V = (wx^2 x^2 + wy^2 y^2)/2, nonlinearities c0 and c2, angular velocity
+ * omeg (OMEG, the Omega of Eq. S.3), SO type (eta = +1 Rashba, -1 Dresselhaus)
+ * and strength gamma, Rabi strength rabi (the R of Eqs. S.1-S.2). */
+typedef struct {
+    int nx, ny;
+    double xlen, ylen;
+    double dt;
+    double wx, wy;
+    double c0, c2, omeg;
+    int so_type;     /* gp_so_type */
+    double gamma, rabi;
+    int precision;   /* gp_precision */
+} gp_params;
+
+/* Observables of the current state (normalisation/magnetisation conditions and
+ * energy functional, Eq. S.6):
+ *   norm[c]      = dx dy sum |psi_c|^2 for c = +1, 0, -1
+ *   norm_total   = sum of the three
+ *   magnetization= norm[0] - norm[2]
+ *   energy       = E of Eq. (S.6), discretised consistently with the sweeps
+ *   mu           = <H_GP> / N (the chemical potential of a stationary state)
+ *   steps        = time steps taken by the handle so far                      */
+typedef struct {
+    double norm[3];
+    double norm_total;
+    double magnetization;
+    double energy;
+    double mu;
+    long long steps;
+} gp_obs;
+
+typedef struct gp_handle gp_handle;
+
+/* Validates params, allocates the device state on the current CUDA device and
+ * returns a handle in *out.  cuda_stream is a cudaStream_t (NULL: the handle
+ * creates its own non-blocking stream).  Fails with GP_ERR_ARG before any
+ * allocation for nx or ny < 4, non-positive or non-finite lengths or dt,
+ * non-finite physical parameters, or an unknown so_type / precision. */
+int gp_create(const gp_params* params, void* cuda_stream, gp_handle** out);
+
+/* Releases every device allocation of h.  NULL is ignored. */
+void gp_destroy(gp_handle* h);
+
+/* Replaces the physical parameters (dt, trap, c0, c2, omeg, SO, rabi) of h,
+ * e.g. for an Omega quench.  The grid (nx, ny, xlen, ylen) and precision must
+ * be unchanged.  The Thomas coefficient tables are rebuilt on the next
+ * propagate call. */
+int gp_set_params(gp_handle* h, const gp_params* params);
+
+/* Copies a host wave function psi[3][ny][nx] (complex128) into h.  If
+ * normalize != 0 it is rescaled on the device so that the total norm is 1. */
+int gp_set_state(gp_handle* h, const double* psi_host, int normalize);
+
+/* Writes the current wave function (complex128, psi[3][ny][nx]) into the
+ * caller's host buffer psi_out.  Any pending imaginary-time normalisation is
+ * applied to the copy. */
+int gp_get_state(gp_handle* h, double* psi_out);
+
+/* Device initial state: psi_c = sqrt(frac[c]) pi^{-1/2} exp(-(x^2+y^2)/2)
+ * exp(i phi_c(x,y)), phi = phase_noise (2u - 1), u = top 53 bits of
+ * splitmix64(seed ^ ((c ny + j) nx + i)) times 2^-53; then normalised to 1. */
+int gp_init_gaussian(gp_handle* h, const double frac[3], unsigned long long seed, double phase_noise);
+
+/* Advances h by nsteps split-step Crank-Nicolson steps: P(dt) -> X(dt) -> Y(dt),
+ * and in imaginary time (mode GP_IMAG) renormalisation to a total norm of 1
+ * after every step.  mode GP_REAL propagates i d_t psi = H psi.  nsteps = 0 is
+ * a no-op. */
+int gp_propagate(gp_handle* h, long long nsteps, int mode);
+
+/* Computes the observables of the current state on the device (FP64, fixed
+ * reduction order, so repeated calls give bitwise identical results).
+ * Returns GP_ERR_NONFINITE (and still fills *out) if psi holds NaN or Inf. */
+int gp_observables(gp_handle* h, gp_obs* out);
+
+/* Test hook: applies one substep to the state, which = 0 (pointwise P),
+ * 1 (X sweep) or 2 (Y sweep), with the time step and mode given, without the
+ * imaginary-time renormalisation and without counting a step. */
+int gp_apply_substep(gp_handle* h, int which, int mode);
+
+/* Human-readable text for a gp_status. */
+const char* gp_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPSPIN_H */
