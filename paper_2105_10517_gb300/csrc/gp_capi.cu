@@ -1,0 +1,439 @@
+// gp_capi.cu -- the C ABI of libgpspin (include/gpspin.h): handle, device
+// state, Thomas coefficient cache, tiling choice and the step sequence of the
+// split-step Crank-Nicolson method (arXiv 2105.10517, program summary "Solution
+// method"; Supplementary Material Eqs. S.1-S.6).
+#include "../../include/gpspin.h"
+#include "gp_internal.cuh"
+
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+
+using namespace gpspin;
+
+namespace {
+
+constexpr int kNormBlocksMax = 4096;
+
+struct CoefSet {
+    bool valid = false;
+    gp_params key{};
+    LineCoef* cx = nullptr;  // [ny][3] x-pass lines (rows)
+    LineCoef* cy = nullptr;  // [nx][3] y-pass lines (columns)
+    double2* ex = nullptr;   // [nx]
+    double2* ey = nullptr;   // [ny]
+    LineTiling tx{}, ty{};
+};
+
+bool same_physics(const gp_params& a, const gp_params& b)
+{
+    return a.dt == b.dt && a.wx == b.wx && a.wy == b.wy && a.omeg == b.omeg && a.so_type == b.so_type &&
+           a.gamma == b.gamma && a.nx == b.nx && a.ny == b.ny && a.xlen == b.xlen && a.ylen == b.ylen;
+}
+
+}  // namespace
+
+struct gp_handle {
+    gp_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    double2* psi = nullptr;    // [3][ny][nx]
+    double2* work = nullptr;   // [3][nx][ny] transposed intermediate / staging
+    double* partials = nullptr;
+    double* obs_part = nullptr;
+    double* scal = nullptr;    // [0] pending normalisation, [1] last norm
+    double* obs_out = nullptr; // [8]
+    int* flag = nullptr;       // bit0 coefficient convergence, bit1 norm, bit2 observables
+    CoefSet coef[2];           // per mode
+    bool scale_pending = false;
+    long long steps = 0;
+};
+
+namespace {
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+int validate(const gp_params* p)
+{
+    if (!p) return GP_ERR_ARG;
+    if (p->nx < 4 || p->ny < 4) return GP_ERR_ARG;
+    if (!(p->xlen > 0) || !(p->ylen > 0) || !(p->dt > 0) || !is_finite(p->xlen) || !is_finite(p->ylen) || !is_finite(p->dt))
+        return GP_ERR_ARG;
+    const double v[] = {p->wx, p->wy, p->c0, p->c2, p->omeg, p->gamma, p->rabi};
+    for (double x : v)
+        if (!is_finite(x)) return GP_ERR_ARG;
+    if (p->so_type < 0 || p->so_type > 2) return GP_ERR_ARG;
+    if (p->precision != GP_FP64) return GP_ERR_ARG;
+    return GP_OK;
+}
+
+int eta_of(const gp_params& p) { return p.so_type == GP_SO_RASHBA ? 1 : (p.so_type == GP_SO_DRESSELHAUS ? -1 : 0); }
+double gamma_of(const gp_params& p) { return p.so_type == GP_SO_NONE ? 0.0 : p.gamma; }
+
+// Largest |c'_inf| over the lines and channels of one direction: the modulus of
+// the smaller root of alpha z^2 - beta z + gamma' = 0 (the fixed point of the
+// Thomas recurrence c'_k = gamma' / (beta - alpha c'_{k-1})).  It fixes how many
+// elements a chunk carry influences above FP64 rounding.
+double max_cp(const gp_params& p, int dir, int mode)
+{
+    typedef std::complex<double> cd;
+    const int nlines = dir == 0 ? p.ny : p.nx;
+    const double h = dir == 0 ? p.xlen / p.nx : p.ylen / p.ny;
+    const double len = dir == 0 ? p.ylen : p.xlen, lh = dir == 0 ? p.ylen / p.ny : p.xlen / p.nx;
+    const cd tau = mode == GP_REAL ? cd(0, 0.5 * p.dt) : cd(0.5 * p.dt, 0);
+    double best = 0;
+    for (int line = 0; line < nlines; ++line) {
+        double pos = -0.5 * len + (line + 0.5) * lh;
+        for (int ch = 0; ch < 3; ++ch) {
+            double lam = 1.0 - ch;
+            double kb = dir == 0 ? gamma_of(p) * lam - p.omeg * pos : p.omeg * pos - eta_of(p) * gamma_of(p) * lam;
+            cd a(-0.5 / (h * h), -kb / (2 * h)), c(-0.5 / (h * h), kb / (2 * h));
+            cd alpha = tau * a, gam = tau * c, beta = 1.0 + tau / (h * h);
+            cd disc = std::sqrt(beta * beta - 4.0 * alpha * gam);
+            cd z1 = (beta - disc) / (2.0 * alpha), z2 = (beta + disc) / (2.0 * alpha);
+            double r = std::min(std::abs(z1), std::abs(z2));
+            if (r > best) best = r;
+        }
+    }
+    return best;
+}
+
+// Chunk length m, fixup length F and lines per CTA for lines of length L.
+int choose_tiling(int L, int nlines, double cpmax, LineTiling* t)
+{
+    if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
+    int F = cpmax > 0 ? (int)std::ceil(60.0 * std::log(2.0) / -std::log(cpmax)) + 1 : 1;
+    int H = (F + 1) / 2 + 2;  // rows until c'_k reaches c'_inf to 2^-60 (contraction |c'|^2 per row)
+    if (F > kFix || H > kHead) return GP_ERR_UNSUPPORTED;
+    int m = std::max(16, H + F);
+    m = (m + 3) / 4 * 4;
+    int Q = (L + m - 1) / m;
+    while (3 * Q > 512) {  // keep one thread per chunk within a CTA
+        m += 4;
+        Q = (L + m - 1) / m;
+    }
+    int Lp = Q * (m + 1) + 1;
+    auto smem_of = [&](int R) { return (size_t)(2 * 3 * R * Lp + 2 * 3 * R * Q) * sizeof(double2); };
+    int R = std::max(1, 256 / (3 * Q));
+    while (R > 1 && (smem_of(R) > 100 * 1024 || 3 * R * Q > 512)) --R;
+    R = std::min(R, nlines);
+    if (smem_of(R) > 227 * 1024) return GP_ERR_UNSUPPORTED;
+    t->L = L;
+    t->nlines = nlines;
+    t->R = R;
+    t->m = m;
+    t->Q = Q;
+    t->F = std::min(F, m - 1);
+    t->Lp = Lp;
+    int thr = std::max(64, 3 * R * Q);
+    t->threads = std::min(512, (thr + 31) / 32 * 32);
+    t->smem = smem_of(R);
+    return GP_OK;
+}
+
+#define CK(x)                                                  \
+    do {                                                       \
+        if (report_cuda((x), #x) != 0) return GP_ERR_CUDA;     \
+    } while (0)
+#define LK(x)                                   \
+    do {                                        \
+        if ((x) != 0) return GP_ERR_CUDA;       \
+    } while (0)
+
+void free_coef(CoefSet& c)
+{
+    cudaFree(c.cx);
+    cudaFree(c.cy);
+    cudaFree(c.ex);
+    cudaFree(c.ey);
+    c = CoefSet{};
+}
+
+int ensure_coef(gp_handle* h, int mode)
+{
+    CoefSet& cs = h->coef[mode];
+    if (cs.valid && same_physics(cs.key, h->p)) return GP_OK;
+    const gp_params& p = h->p;
+    LineTiling tx, ty;
+    int st = choose_tiling(p.nx, p.ny, max_cp(p, 0, mode), &tx);
+    if (st) return st;
+    st = choose_tiling(p.ny, p.nx, max_cp(p, 1, mode), &ty);
+    if (st) return st;
+    if (!cs.cx) {
+        if (cudaMalloc(&cs.cx, sizeof(LineCoef) * 3 * (size_t)p.ny) != cudaSuccess ||
+            cudaMalloc(&cs.cy, sizeof(LineCoef) * 3 * (size_t)p.nx) != cudaSuccess ||
+            cudaMalloc(&cs.ex, sizeof(double2) * p.nx) != cudaSuccess ||
+            cudaMalloc(&cs.ey, sizeof(double2) * p.ny) != cudaSuccess) {
+            free_coef(cs);
+            return GP_ERR_OOM;
+        }
+    }
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    const double dx = p.xlen / p.nx, dy = p.ylen / p.ny;
+    LK(launch_coef(cs.cx, p.ny, 0, mode, dx, p.ylen, dy, p.dt, p.omeg, gamma_of(p), eta_of(p), h->flag, h->stream));
+    LK(launch_coef(cs.cy, p.nx, 1, mode, dy, p.xlen, dx, p.dt, p.omeg, gamma_of(p), eta_of(p), h->flag, h->stream));
+    LK(launch_trap_table(cs.ex, p.nx, p.xlen, p.wx, p.dt, mode, h->stream));
+    LK(launch_trap_table(cs.ey, p.ny, p.ylen, p.wy, p.dt, mode, h->stream));
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (flag & 1) return GP_ERR_UNSUPPORTED;
+    cs.tx = tx;
+    cs.ty = ty;
+    cs.key = p;
+    cs.valid = true;
+    return GP_OK;
+}
+
+PassArgs pass_args(gp_handle* h, const CoefSet& cs, int dir)
+{
+    PassArgs a{};
+    a.nx = h->p.nx;
+    a.ny = h->p.ny;
+    a.scale = h->scal;
+    a.dt = h->p.dt;
+    a.c0 = h->p.c0;
+    a.c2 = h->p.c2;
+    a.rabi = h->p.rabi;
+    a.ex = cs.ex;
+    a.ey = cs.ey;
+    a.do_p = 1;
+    a.do_solve = 1;
+    if (dir == 0) {
+        a.in = h->psi;
+        a.out = h->work;
+        a.coef = cs.cx;
+        a.t = cs.tx;
+    } else {
+        a.in = h->work;
+        a.out = h->psi;
+        a.coef = cs.cy;
+        a.t = cs.ty;
+    }
+    return a;
+}
+
+size_t n_elems(const gp_handle* h) { return 3 * (size_t)h->p.nx * h->p.ny; }
+double cell(const gp_handle* h) { return (h->p.xlen / h->p.nx) * (h->p.ylen / h->p.ny); }
+
+int norm_blocks(const gp_handle* h)
+{
+    size_t n = n_elems(h);
+    size_t b = (n + 255) / 256;
+    return (int)std::min<size_t>(std::max<size_t>(b, 1), 608);
+}
+
+// Makes the stored state the true state (no pending normalisation).
+int flush_scale(gp_handle* h)
+{
+    if (!h->scale_pending) return GP_OK;
+    LK(launch_apply_scale(h->psi, n_elems(h), h->scal, h->stream));
+    h->scale_pending = false;
+    return GP_OK;
+}
+
+int sync_status(gp_handle* h)
+{
+    CK(cudaStreamSynchronize(h->stream));
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gp_strerror(int s)
+{
+    switch (s) {
+    case GP_OK: return "ok";
+    case GP_ERR_ARG: return "invalid argument";
+    case GP_ERR_OOM: return "device allocation failed";
+    case GP_ERR_CUDA: return "CUDA runtime error";
+    case GP_ERR_NONFINITE: return "non-finite values in the wave function";
+    case GP_ERR_UNSUPPORTED: return "parameters outside the supported range of the tabulated line solver";
+    default: return "unknown status";
+    }
+}
+
+int gp_create(const gp_params* params, void* cuda_stream, gp_handle** out)
+{
+    if (!out) return GP_ERR_ARG;
+    *out = nullptr;
+    int st = validate(params);
+    if (st) return st;
+    gp_handle* h = new (std::nothrow) gp_handle();
+    if (!h) return GP_ERR_OOM;
+    h->p = *params;
+    cudaGetDevice(&h->device);
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return GP_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    size_t n = n_elems(h);
+    bool ok = cudaMalloc(&h->psi, n * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&h->work, n * sizeof(double2)) == cudaSuccess &&
+              cudaMalloc(&h->partials, kNormBlocksMax * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&h->obs_part, (size_t)obs_blocks(h->p.nx, h->p.ny) * obs_slots() * sizeof(double)) ==
+                  cudaSuccess &&
+              cudaMalloc(&h->scal, 2 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&h->obs_out, 8 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&h->flag, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        gp_destroy(h);
+        return GP_ERR_OOM;
+    }
+    if (cudaMemsetAsync(h->psi, 0, n * sizeof(double2), h->stream) != cudaSuccess ||
+        launch_set_scalar(h->scal, 1.0, h->stream) != 0 || cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        gp_destroy(h);
+        return GP_ERR_CUDA;
+    }
+    *out = h;
+    return GP_OK;
+}
+
+void gp_destroy(gp_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& c : h->coef) free_coef(c);
+    cudaFree(h->psi);
+    cudaFree(h->work);
+    cudaFree(h->partials);
+    cudaFree(h->obs_part);
+    cudaFree(h->scal);
+    cudaFree(h->obs_out);
+    cudaFree(h->flag);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int gp_set_params(gp_handle* h, const gp_params* params)
+{
+    if (!h) return GP_ERR_ARG;
+    int st = validate(params);
+    if (st) return st;
+    if (params->nx != h->p.nx || params->ny != h->p.ny || params->xlen != h->p.xlen || params->ylen != h->p.ylen ||
+        params->precision != h->p.precision)
+        return GP_ERR_ARG;
+    h->p = *params;
+    return GP_OK;
+}
+
+int gp_set_state(gp_handle* h, const double* psi_host, int normalize)
+{
+    if (!h || !psi_host) return GP_ERR_ARG;
+    CK(cudaMemcpyAsync(h->psi, psi_host, n_elems(h) * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+    LK(launch_set_scalar(h->scal, 1.0, h->stream));
+    h->scale_pending = false;
+    if (normalize) {
+        CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+        LK(launch_norm(h->psi, n_elems(h), h->partials, norm_blocks(h), cell(h), h->scal, h->flag, h->stream));
+        h->scale_pending = true;
+        int flag = 0;
+        CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (flag & 2) return GP_ERR_NONFINITE;
+    }
+    return sync_status(h);
+}
+
+int gp_get_state(gp_handle* h, double* psi_out)
+{
+    if (!h || !psi_out) return GP_ERR_ARG;
+    LK(launch_scaled_copy(h->work, h->psi, n_elems(h), h->scal, h->stream));
+    CK(cudaMemcpyAsync(psi_out, h->work, n_elems(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
+    return sync_status(h);
+}
+
+int gp_init_gaussian(gp_handle* h, const double frac[3], unsigned long long seed, double phase_noise)
+{
+    if (!h || !frac || !is_finite(phase_noise)) return GP_ERR_ARG;
+    for (int c = 0; c < 3; ++c)
+        if (!(frac[c] >= 0) || !is_finite(frac[c])) return GP_ERR_ARG;
+    LK(launch_init_gaussian(h->psi, h->p.nx, h->p.ny, h->p.xlen, h->p.ylen, frac, seed, phase_noise, h->stream));
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    LK(launch_norm(h->psi, n_elems(h), h->partials, norm_blocks(h), cell(h), h->scal, h->flag, h->stream));
+    h->scale_pending = true;
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return (flag & 2) ? GP_ERR_NONFINITE : GP_OK;
+}
+
+int gp_propagate(gp_handle* h, long long nsteps, int mode)
+{
+    if (!h || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
+    if (nsteps == 0) return GP_OK;
+    int st = ensure_coef(h, mode);
+    if (st) return st;
+    const CoefSet& cs = h->coef[mode];
+    if (mode == GP_REAL && (st = flush_scale(h))) return st;
+    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+    if (mode == GP_IMAG) {
+        int gy = (cs.ty.nlines + cs.ty.R - 1) / cs.ty.R;
+        if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
+        ay.partials = h->partials;
+        CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+        for (long long s = 0; s < nsteps; ++s) {
+            LK(launch_xpass(ax, mode, h->stream));
+            LK(launch_ypass(ay, mode, h->stream));
+            LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
+        }
+        h->scale_pending = true;
+    } else {
+        for (long long s = 0; s < nsteps; ++s) {
+            LK(launch_xpass(ax, mode, h->stream));
+            LK(launch_ypass(ay, mode, h->stream));
+        }
+    }
+    h->steps += nsteps;
+    return sync_status(h);
+}
+
+int gp_apply_substep(gp_handle* h, int which, int mode)
+{
+    if (!h || which < 0 || which > 2 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
+    int st = ensure_coef(h, mode);
+    if (st) return st;
+    if ((st = flush_scale(h))) return st;
+    const CoefSet& cs = h->coef[mode];
+    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+    ax.do_p = which == 0;
+    ax.do_solve = which == 1;
+    ay.do_solve = which == 2;
+    LK(launch_xpass(ax, mode, h->stream));
+    LK(launch_ypass(ay, mode, h->stream));
+    return sync_status(h);
+}
+
+int gp_observables(gp_handle* h, gp_obs* out)
+{
+    if (!h || !out) return GP_ERR_ARG;
+    const gp_params& p = h->p;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    LK(launch_observables(h->psi, h->scal, p.nx, p.ny, p.xlen, p.ylen, p.wx, p.wy, p.c0, p.c2, p.rabi, p.omeg,
+                          gamma_of(p), eta_of(p), h->obs_part, h->obs_out, h->flag, h->stream));
+    double v[8];
+    int flag = 0;
+    CK(cudaMemcpyAsync(v, h->obs_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    out->norm[0] = v[0];
+    out->norm[1] = v[1];
+    out->norm[2] = v[2];
+    out->norm_total = v[3];
+    out->magnetization = v[4];
+    out->energy = v[5];
+    out->mu = v[6];
+    out->steps = h->steps;
+    return (flag & 4) ? GP_ERR_NONFINITE : GP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// gp_internal.cuh -- data layout and launch arguments shared by the CUDA
+// translation units of libgpspin (not part of the public C ABI).
+//
+// One split-step Crank-Nicolson time step (arXiv 2105.10517, program summary
+// "Solution method"; Supplementary Material Eqs. S.1-S.5) is two line passes:
+//
+//   x-pass  psi[c][j][i] --(pending scale s, pointwise substep P, U_y^dagger)-->
+//           Sigma_y eigen-channels --(CN solve along x per row and channel)-->
+//           --(U_x^dagger U_y)--> Sigma_x eigen-channels, stored TRANSPOSED as
+//           t[mu][i][j] so that the y-pass reads whole columns contiguously;
+//   y-pass  t[mu][i][j] --(CN solve along y per column and channel)--(U_x)-->
+//           psi[c][j][i] plus per-CTA partial norms (FP64).
+//
+// In imaginary time a one-CTA kernel turns the partial norms into the scale
+// s = 1/sqrt(N) that the next x-pass applies on load ("pending" scale).
+//
+// The SO term gamma(eta p_y Sigma_x - p_x Sigma_y) is diagonalised by the
+// constant unitaries U_y (eigenvectors of Sigma_y) in the x-pass and U_x
+// (eigenvectors of Sigma_x) in the y-pass, so each line system is a scalar
+// tridiagonal per channel lambda in {+1, 0, -1}:
+//   A = -1/2 D2 + kappa D1,  kappa = i(gamma lambda - Omega y_j)      (x-pass)
+//                            kappa = i(Omega x_i - eta gamma mu)       (y-pass)
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace gpspin {
+
+// Head length of the tabulated Thomas factorisation and of the fixup powers.
+constexpr int kHead = 32;
+constexpr int kFix = 64;
+
+// Thomas factorisation of (I + tau A) for one line and one eigen-channel.
+// Row k of the elimination: inv_k = 1/(beta - alpha c'_{k-1}), c'_k = gamma' inv_k,
+// g_k = alpha inv_k.  Entries k >= kHead equal entry kHead-1 to FP64 rounding
+// (the recurrence contracts by |c'|^2 per row), so kernels index min(k, kHead-1).
+// pf[t] = (-g_inf)^(t+1) and pb[t] = (-c'_inf)^(t+1) are the influence of a
+// chunk's carry on the t-th element after (forward) or before (backward) it.
+struct LineCoef {
+    double2 inv[kHead];
+    double2 g[kHead];
+    double2 cp[kHead];
+    double2 pf[kFix];
+    double2 pb[kFix];
+};
+
+// Tiling of one line pass (chosen on the host).
+struct LineTiling {
+    int L;      // line length
+    int nlines; // number of lines
+    int R;      // lines per CTA
+    int m;      // chunk length of the parallel Thomas solve
+    int Q;      // chunks per line = ceil(L / m)
+    int F;      // fixup length (|c'_inf|^F <= 2^-60), F < m
+    int Lp;     // padded smem stride of one line-channel: Q (m + 1) + 1
+    int threads;
+    size_t smem;
+};
+
+struct PassArgs {
+    const double2* in;
+    double2* out;
+    const LineCoef* coef;      // [nlines][3]
+    LineTiling t;
+    int nx, ny;
+    int do_p;                  // x-pass: apply the pointwise substep
+    int do_solve;              // apply the CN solve (0: channels pass through)
+    const double* scale;       // device scalar: pending normalisation (x-pass)
+    double* partials;          // y-pass: per-CTA sum |psi|^2
+    // pointwise substep constants (x-pass)
+    const double2* ex;         // [nx] exp(-tau' wx^2 x^2 / 2)
+    const double2* ey;         // [ny] exp(-tau' wy^2 y^2 / 2)
+    double dt, c0, c2, rabi;
+};
+
+}  // namespace gpspin
+
+namespace gpspin {
+int report_cuda(cudaError_t e, const char* what);
+// launchers (gp_sweeps.cu)
+int launch_coef(LineCoef* coef, int nlines, int dir, int mode, double h, double line_len, double line_h,
+                double dt, double omeg, double gamma, int eta, int* status, cudaStream_t st);
+int launch_trap_table(double2* out, int n, double len, double w, double dt, int mode, cudaStream_t st);
+int launch_xpass(const PassArgs& a, int mode, cudaStream_t st);
+int launch_ypass(const PassArgs& a, int mode, cudaStream_t st);
+// launchers (gp_reduce.cu)
+int launch_norm(const double2* psi, size_t n, double* partials, int nblk, double da, double* scale, int* flag,
+                cudaStream_t st);
+int launch_finalize_norm(const double* partials, int n, double da, double* scale, int* flag, cudaStream_t st);
+int launch_apply_scale(double2* psi, size_t n, double* scale, cudaStream_t st);
+int launch_set_scalar(double* p, double v, cudaStream_t st);
+int launch_scaled_copy(double2* dst, const double2* src, size_t n, const double* scale, cudaStream_t st);
+int launch_init_gaussian(double2* psi, int nx, int ny, double xlen, double ylen, const double frac[3],
+                         unsigned long long seed, double noise, cudaStream_t st);
+int obs_blocks(int nx, int ny);
+int obs_slots();
+int launch_observables(const double2* psi, const double* scale, int nx, int ny, double xlen, double ylen, double wx,
+                       double wy, double c0, double c2, double rabi, double omeg, double gamma, int eta,
+                       double* partials, double* out, int* flag, cudaStream_t st);
+}  // namespace gpspin

@@ -1,0 +1,226 @@
+"""Python binding of libgpspin (include/gpspin.h): argument marshalling only.
+
+Every step of the split-step Crank-Nicolson method runs in the CUDA library;
+this module builds it in-tree for sm_103a, loads it with ctypes and converts
+numpy arrays and parameter dicts.  There is no CPU fallback: if the library is
+missing or fails to load, every entry point raises.
+"""
+import ctypes
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+LIB_PATH = os.path.join(PKG, "libgpspin.so")
+BUILD_DIR = os.path.join(PKG, "_build")
+SOURCES = ["gp_capi.cu", "gp_sweeps.cu", "gp_reduce.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
+
+IMAG, REAL = 0, 1
+SO_NONE, SO_RASHBA, SO_DRESSELHAUS = 0, 1, 2
+FP64 = 0
+SUB_P, SUB_X, SUB_Y = 0, 1, 2
+
+STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP_ERR_NONFINITE",
+          5: "GP_ERR_UNSUPPORTED"}
+
+# Every symbol the public header declares (checked by the CPU tests).
+EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
+           "gp_propagate", "gp_observables", "gp_apply_substep", "gp_strerror"]
+
+
+def _nvcc():
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def _stale(lib, deps):
+    if not os.path.exists(lib):
+        return True
+    t = os.path.getmtime(lib)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force=False, verbose=False):
+    """Compile the CUDA sources (in parallel, one -gencode for sm_103a) and link
+    libgpspin.so next to this file.  Returns the library path."""
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "gp_internal.cuh"),
+                                                        os.path.join(ROOT, "include", "gpspin.h")]
+    if not force and not _stale(LIB_PATH, deps):
+        return LIB_PATH
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    nvcc = _nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(BUILD_DIR, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc] + NVCC_FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose and r.stderr:
+            sys.stderr.write(r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + ".tmp"
+    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("xlen", ctypes.c_double), ("ylen", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("wx", ctypes.c_double), ("wy", ctypes.c_double),
+        ("c0", ctypes.c_double), ("c2", ctypes.c_double), ("omeg", ctypes.c_double),
+        ("so_type", ctypes.c_int),
+        ("gamma", ctypes.c_double), ("rabi", ctypes.c_double),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [
+        ("norm", ctypes.c_double * 3),
+        ("norm_total", ctypes.c_double),
+        ("magnetization", ctypes.c_double),
+        ("energy", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("steps", ctypes.c_longlong),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libgpspin.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2105_10517_gb300.gpspin.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.gp_create.argtypes = [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+    lib.gp_destroy.argtypes = [vp]
+    lib.gp_destroy.restype = None
+    lib.gp_set_params.argtypes = [vp, ctypes.POINTER(Params)]
+    lib.gp_set_state.argtypes = [vp, dp, ip]
+    lib.gp_get_state.argtypes = [vp, dp]
+    lib.gp_init_gaussian.argtypes = [vp, dp, ctypes.c_ulonglong, ctypes.c_double]
+    lib.gp_propagate.argtypes = [vp, ctypes.c_longlong, ip]
+    lib.gp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
+    lib.gp_apply_substep.argtypes = [vp, ip, ip]
+    lib.gp_strerror.argtypes = [ip]
+    lib.gp_strerror.restype = ctypes.c_char_p
+    for name in ("gp_create", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
+                 "gp_propagate", "gp_observables", "gp_apply_substep"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class GPError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        msg = load().gp_strerror(status).decode()
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({msg})")
+
+
+def _check(st, what):
+    if st != 0:
+        raise GPError(st, what)
+
+
+PARAM_DEFAULTS = dict(wx=1.0, wy=1.0, c0=0.0, c2=0.0, omeg=0.0, so_type=0, gamma=0.0, rabi=0.0, precision=FP64)
+
+
+def make_params(p):
+    q = dict(PARAM_DEFAULTS)
+    q.update({k: v for k, v in p.items() if k in Params.__dict__ or k in dict(Params._fields_)})
+    return Params(int(q["nx"]), int(q["ny"]), float(q["xlen"]), float(q["ylen"]), float(q["dt"]),
+                  float(q["wx"]), float(q["wy"]), float(q["c0"]), float(q["c2"]), float(q["omeg"]),
+                  int(q["so_type"]), float(q["gamma"]), float(q["rabi"]), int(q["precision"]))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Solver:
+    """One GP instance on the current CUDA device (a gp_handle)."""
+
+    def __init__(self, params, stream=None):
+        lib = load()
+        self.params = dict(params)
+        self._p = make_params(params)
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(int(stream)) if stream is not None else None
+        _check(lib.gp_create(ctypes.byref(self._p), s, ctypes.byref(h)), "gp_create")
+        self._h = h
+        self.nx, self.ny = self._p.nx, self._p.ny
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, params):
+        p = make_params(params)
+        _check(load().gp_set_params(self._h, ctypes.byref(p)), "gp_set_params")
+        self.params = dict(params)
+        self._p = p
+
+    def set_state(self, psi, normalize=False):
+        a = np.ascontiguousarray(psi, dtype=np.complex128)
+        if a.shape != (3, self.ny, self.nx):
+            raise ValueError(f"psi must have shape (3, {self.ny}, {self.nx})")
+        _check(load().gp_set_state(self._h, _dptr(a), int(bool(normalize))), "gp_set_state")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((3, self.ny, self.nx), dtype=np.complex128)
+        _check(load().gp_get_state(self._h, _dptr(out)), "gp_get_state")
+        return out
+
+    def init_gaussian(self, frac=(0.25, 0.5, 0.25), seed=1, phase_noise=1e-3):
+        f = np.asarray(frac, dtype=np.float64)
+        _check(load().gp_init_gaussian(self._h, _dptr(f), int(seed), float(phase_noise)), "gp_init_gaussian")
+
+    def propagate(self, nsteps, mode=IMAG):
+        _check(load().gp_propagate(self._h, int(nsteps), int(mode)), "gp_propagate")
+
+    def apply_substep(self, which, mode=IMAG):
+        w = {"P": SUB_P, "X": SUB_X, "Y": SUB_Y}.get(which, which)
+        _check(load().gp_apply_substep(self._h, int(w), int(mode)), "gp_apply_substep")
+
+    def observables(self):
+        o = Obs()
+        _check(load().gp_observables(self._h, ctypes.byref(o)), "gp_observables")
+        return dict(norm=np.array(o.norm[:]), norm_total=o.norm_total, magnetization=o.magnetization,
+                    energy=o.energy, mu=o.mu, steps=o.steps)

@@ -1,0 +1,56 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, and exports every
+function the public header declares (no device calls: there may be no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2105_10517_gb300 import gpspin
+
+HEADER = os.path.join(gpspin.ROOT, "include", "gpspin.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gp_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gpspin.build()
+    return ctypes.CDLL(gpspin.LIB_PATH)
+
+
+def test_header_declares_the_binding_exports():
+    assert header_functions() == sorted(gpspin.EXPORTS)
+
+
+def test_library_exports_every_header_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_strerror_needs_no_device(lib):
+    lib.gp_strerror.restype = ctypes.c_char_p
+    lib.gp_strerror.argtypes = [ctypes.c_int]
+    assert lib.gp_strerror(0) == b"ok"
+    assert b"invalid" in lib.gp_strerror(1)
+
+
+def test_create_rejects_invalid_parameters_before_any_device_call(lib):
+    lib = gpspin.load()
+    h = ctypes.c_void_p()
+    for bad in (dict(nx=3), dict(dt=0.0), dict(xlen=-1.0), dict(so_type=7), dict(c0=float("nan")), dict(precision=9)):
+        p = dict(nx=16, ny=16, xlen=8.0, ylen=8.0, dt=0.01)
+        p.update(bad)
+        assert lib.gp_create(ctypes.byref(gpspin.make_params(p)), None, ctypes.byref(h)) == 1
+    assert lib.gp_create(None, None, ctypes.byref(h)) == 1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(gpspin, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(gpspin, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        gpspin.load()

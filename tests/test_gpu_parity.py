@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: single substeps and short runs agree to 1e-12 (rounding order only:
+the oracle solves 3x3-block systems in the original spin basis, the GPU solves
+scalar systems per eigen-channel); after 1000 steps max|dpsi| <= 1e-10 and
+|dE/E| <= 1e-12.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_10517_gb300 import gpspin, inputs
+
+pytestmark = pytest.mark.gpu
+
+IMAG, REAL = gpspin.IMAG, gpspin.REAL
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    gpspin.build()
+    gpspin.load()
+
+
+def ragged(**kw):
+    # 72 x 45: several chunks per line plus a ragged last chunk in both directions
+    p = dict(nx=72, ny=45, xlen=14.4, ylen=9.9, dt=0.004, wx=1.0, wy=1.2, c0=60.0, c2=-6.0, omeg=0.7,
+             so_type=1, gamma=0.8, rabi=0.35)
+    p.update(kw)
+    return p
+
+
+def smooth_plus_rough(p, seed):
+    g = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=seed, phase_noise=0.3)
+    return g + inputs.random_state(p["nx"], p["ny"], seed=seed + 100, scale=0.05)
+
+
+@pytest.mark.parametrize("mode", [IMAG, REAL])
+@pytest.mark.parametrize("so_type", [0, 1, 2])
+@pytest.mark.parametrize("which", ["P", "X", "Y"])
+def test_substep_parity(which, so_type, mode):
+    p = ragged(so_type=so_type)
+    psi = smooth_plus_rough(p, 3 + so_type)
+    want = oracle.substep(p, psi, which, mode)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        s.apply_substep(which, mode)
+        got = s.get_state()
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(got - want)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("mode", [IMAG, REAL])
+def test_substep_parity_large_arguments(mode):
+    # dt c0 rho > 1/8 and dt |B| > 0.1: the library-function branches of P
+    p = ragged(c0=4000.0, c2=-900.0, rabi=40.0, dt=0.01)
+    psi = smooth_plus_rough(p, 9)
+    want = oracle.substep(p, psi, "P", mode)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        s.apply_substep("P", mode)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("mode", [IMAG, REAL])
+def test_short_run_parity(mode):
+    p = ragged()
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=5)
+    want = oracle.propagate(p, psi, 20, mode)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        s.propagate(20, mode)
+        got = s.get_state()
+        obs = s.observables()
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    o = oracle.observables(p, want)
+    assert abs(obs["energy"] - o["energy"]) <= 1e-12 * abs(o["energy"])
+
+
+def test_observables_parity():
+    for so_type in (0, 1, 2):
+        p = ragged(so_type=so_type)
+        psi = smooth_plus_rough(p, 21 + so_type)
+        o = oracle.observables(p, psi)
+        with gpspin.Solver(p) as s:
+            s.set_state(psi)
+            g = s.observables()
+        for k in ("norm_total", "magnetization", "energy", "mu"):
+            assert abs(g[k] - o[k]) <= 1e-12 * max(1.0, abs(o[k])), k
+        assert np.allclose(g["norm"], o["norm"], rtol=1e-13, atol=0)
+
+
+def test_init_gaussian_matches_input_generator():
+    p = ragged()
+    want = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], frac=(0.25, 0.5, 0.25), seed=77,
+                                 phase_noise=1e-3)
+    with gpspin.Solver(p) as s:
+        s.init_gaussian((0.25, 0.5, 0.25), seed=77, phase_noise=1e-3)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 1e-15
+
+
+def test_thousand_step_parity_small64():
+    """The 64 x 64 imaginary-time workload: 1000 steps, max|dpsi| <= 1e-10, |dE/E| <= 1e-12."""
+    c = inputs.CONFIGS["small64"]
+    p = inputs.physics(c)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=c["seed"])
+    want = oracle.propagate(p, psi, 1000, IMAG)
+    with gpspin.Solver(p) as s:
+        s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+        s.propagate(1000, IMAG)
+        got = s.get_state()
+        e = s.observables()["energy"]
+    eo = oracle.observables(p, want)["energy"]
+    assert np.max(np.abs(got - want)) <= 1e-10
+    assert abs(e - eo) <= 1e-12 * abs(eo)
+
+
+def test_real_time_parity_and_norm():
+    p = ragged(so_type=2, nx=48, ny=40, xlen=12.0, ylen=10.0, dt=0.002)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=8)
+    want = oracle.propagate(p, psi, 300, REAL)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        s.propagate(300, REAL)
+        got = s.get_state()
+        obs = s.observables()
+    assert np.max(np.abs(got - want)) <= 1e-11
+    assert abs(obs["norm_total"] - 1.0) <= 1e-12
+
+
+def test_rashba_dresselhaus_mirror_on_gpu():
+    p = ragged(nx=40, ny=36, xlen=10.0, ylen=9.0)
+    psi = smooth_plus_rough(p, 31)
+    with gpspin.Solver(dict(p, so_type=1, omeg=0.6)) as a, gpspin.Solver(dict(p, so_type=2, omeg=-0.6)) as b:
+        a.set_state(psi)
+        b.set_state(psi[:, ::-1, :].copy())
+        a.propagate(50, IMAG)
+        b.propagate(50, IMAG)
+        ga, gb = a.get_state(), b.get_state()
+        ea, eb = a.observables()["energy"], b.observables()["energy"]
+    assert np.max(np.abs(ga[:, ::-1, :] - gb)) <= 1e-12
+    assert abs(ea - eb) <= 1e-12 * abs(ea)
+
+
+@pytest.mark.parametrize("shape", [(4, 4), (5, 9), (130, 17), (17, 130)])
+def test_edge_shapes(shape):
+    nx, ny = shape
+    p = ragged(nx=nx, ny=ny, xlen=0.2 * nx, ylen=0.2 * ny)
+    psi = smooth_plus_rough(p, 41)
+    want = oracle.propagate(p, psi, 3, IMAG)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        s.propagate(3, IMAG)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def test_full_size_vortex512_sampled():
+    """The 512 x 512 workload in the launch configuration the benchmark times:
+    two steps compared everywhere (the oracle finishes them in seconds)."""
+    c = inputs.CONFIGS["vortex512"]
+    p = inputs.physics(c)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=c["seed"])
+    want = oracle.propagate(p, psi, 2, IMAG)
+    with gpspin.Solver(p) as s:
+        s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+        s.propagate(2, IMAG)
+        got = s.get_state()
+        e = s.observables()["energy"]
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    assert abs(e - oracle.observables(p, want)["energy"]) <= 1e-12 * abs(e)
+
+
+def test_determinism_bitwise():
+    p = ragged()
+    out = []
+    for _ in range(2):
+        with gpspin.Solver(p) as s:
+            s.init_gaussian(seed=3)
+            s.propagate(25, IMAG)
+            out.append((s.get_state(), s.observables()["energy"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_errors_are_reported():
+    p = ragged()
+    with gpspin.Solver(p) as s:
+        bad = smooth_plus_rough(p, 1)
+        bad[1, 3, 4] = np.nan
+        with pytest.raises(gpspin.GPError) as ei:
+            s.set_state(bad, normalize=True)
+        assert ei.value.status == 4
+        with pytest.raises(gpspin.GPError):
+            s.propagate(-1)
+        with pytest.raises(gpspin.GPError):
+            s.set_params(dict(p, nx=10))
+    # dt far beyond the tabulated factorisation's range
+    with gpspin.Solver(ragged(dt=50.0)) as s:
+        s.init_gaussian()
+        with pytest.raises(gpspin.GPError) as ei:
+            s.propagate(1)
+        assert ei.value.status == 5
+
+
+def test_omega_quench_rebuilds_coefficients():
+    p = ragged()
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=12)
+    q = dict(p, omeg=0.9)
+    want = oracle.propagate(q, oracle.propagate(p, psi, 5, REAL), 5, REAL)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        s.propagate(5, REAL)
+        s.set_params(q)
+        s.propagate(5, REAL)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
