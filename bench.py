@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the split-step Crank-Nicolson step (one JSON line on rank 0).
+
+A bench step is one time step of the whole hot path: pending normalisation,
+pointwise substep P, X sweep, Y sweep and the imaginary-time renormalisation,
+on the 512 x 512 imaginary-time vortex-lattice workload ([-16,16]^2, dt = 1e-3,
+c0 = 500, c2 = -10, Omega = 0.8, Rashba gamma = 1, R = 0) from its seeded
+Gaussian initial state.  The metric is site-steps per second (one grid point
+advanced one full step, all three components).
+
+  python bench.py [--gpus N --steps K --warmup W]   the CUDA path (C ABI)
+  python bench.py --impl reference ...              the FP64 CPU oracle
+
+Under torchrun (N > 1) the path does not shard: every rank advances its own
+replica (weak scaling), and the value is all ranks' site-steps over the slowest
+rank's time.  The reference arm runs on rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Msite-steps/s & %HBM peak; served solves/s, p50/p99 vs plain FP64 at ΔE/E≤1e-6"
+UNIT = "Msite-steps/s"
+WORKLOAD = "vortex512"
+
+# Roofline of the FP64 path: it is bound by FP64 issue, not HBM.  GB300 retires
+# 2 FP64 FMA lanes per SM per clock (measured 1.2 TFLOP/s, rate independent of
+# how many lanes of a warp are active): 2 lanes x 2 flop x 152 SMs x 2.07 GHz.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+# Algorithmic FP64 flops per site (FMA = 2) of the two line passes in imaginary
+# time, small-argument branches, counted from the kernel arithmetic:
+#   x-pass: P 182 (73 FMA, 33 MUL, 3 ADD) + U_y^dag 16 + Thomas 3 x 26 + U_x^dag U_y 14
+#   y-pass: Thomas 3 x 26 + U_x 16 + |psi|^2 partial sums 12
+FLOPS_PER_SITE = {"xpass": 290, "ypass": 106}
+INST_PER_SITE = {"xpass": 177, "ypass": 63}
+# Algorithmic HBM bytes per site and pass: read and write 3 complex128 values.
+BYTES_PER_SITE_PASS = 96
+# DRAM traffic of one launch from an ncu capture (profiles/), keyed by kernel
+# and valid only while the kernel source is unchanged (sha256 prefix).
+NCU_TRAFFIC = {}
+
+L2_FLUSH_BYTES = 256 << 20
+
+
+def sha_kernels():
+    h = hashlib.sha256()
+    for f in ("gp_sweeps.cu", "gp_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2105_10517_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2105_10517_gb300 import inputs
+    c = dict(inputs.CONFIGS[WORKLOAD])
+    return c, inputs.physics(c)
+
+
+def config_dict(c):
+    return {
+        "workload": f"{WORKLOAD}: {c['nx']}x{c['ny']} imaginary-time vortex lattice, [-16,16]^2, dt={c['dt']}, "
+                    f"c0={c['c0']}, c2={c['c2']}, Omega={c['omeg']}, Rashba gamma={c['gamma']}, R={c['rabi']}",
+        "nx": c["nx"], "ny": c["ny"], "dt": c["dt"], "mode": "imaginary",
+        "step": "one split-step CN time step: normalise, P, X sweep, Y sweep, norm",
+        "l2": "flushed by a 256 MiB device write before every timed step",
+        "parallelism": "replicas",
+    }
+
+
+# --------------------------------------------------------------- clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ our arm -----
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2105_10517_gb300 import gpspin, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    gpspin.build()
+    c, p = workload()
+    sites = c["nx"] * c["ny"]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    s = gpspin.Solver(p, stream=stream.cuda_stream)
+    s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+    for _ in range(max(3, args.warmup)):
+        s.profile_step(gpspin.IMAG)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t0 = time.perf_counter()
+    per = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        per.append(s.profile_step(gpspin.IMAG))
+    barrier()
+    wall = time.perf_counter() - t0
+    # keep the GPU busy until the sampler has seen the load a few times
+    t1 = time.perf_counter()
+    while len(clocks.lines) < 5 and time.perf_counter() - t1 < 3.0:
+        s.propagate(20, gpspin.IMAG)
+    clocks.stop()
+
+    ms_x = statistics.fmean(q[0] for q in per)
+    ms_y = statistics.fmean(q[1] for q in per)
+    ms_n = statistics.fmean(q[2] for q in per)
+    ms_step = statistics.fmean(q[3] for q in per)
+    total_ms = ms_step * args.steps
+    t_max = total_ms
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * sites * args.steps / (t_max / 1e3) / 1e6
+
+    # end to end through the public API with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        psi0 = inputs.gaussian_state(c["nx"], c["ny"], p["xlen"], p["ylen"], seed=c["seed"])
+        hin = torch.from_numpy(psi0).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        for _ in range(3):
+            s.set_state(hin)
+            s.propagate(1, gpspin.IMAG)
+            s.get_state(hout)
+        barrier()
+        te = time.perf_counter()
+        a, b = hin, hout
+        for _ in range(args.e2e_steps):
+            s.set_state(a)
+            s.propagate(1, gpspin.IMAG)
+            s.get_state(b)
+            a, b = b, a
+        barrier()
+        el = time.perf_counter() - te
+        if dist:
+            tt = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        nbytes = 3 * sites * 16
+        e2e = {"value": world * sites * args.e2e_steps / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
+               "path": "gp_set_state(pinned) + gp_propagate(1) + gp_get_state(pinned) per step"}
+
+    dom = "xpass" if ms_x >= ms_y else "ypass"
+    ms_dom = ms_x if dom == "xpass" else ms_y
+    achieved = FLOPS_PER_SITE[dom] * sites / (ms_dom / 1e3) / 1e12
+    key = f"{dom}_kernel<0> {WORKLOAD}"
+    tr = NCU_TRAFFIC.get(key)
+    traffic = tr[0] if tr and tr[1] == sha_kernels() else None
+    roofline = {
+        "bound": "alu", "kernel": f"{dom}_kernel<0> (FP64)", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+        "peak_source": "derived: 2 FP64 FMA lanes/SM/clk x 152 SMs x 2.07 GHz x 2 flop",
+        "fp64_issue_frac": INST_PER_SITE[dom] * sites / (ms_dom / 1e3) / (FP64_PEAK_TFLOPS / 2 * 1e12),
+        "flops_per_launch": FLOPS_PER_SITE[dom] * sites, "traffic": traffic,
+        "hbm_frac_of_measured": None,
+        "kernel_ms": {"xpass": ms_x, "ypass": ms_y, "normalise": ms_n},
+    }
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks["hbm_gbs"])
+        roofline["hbm_frac_of_measured"] = BYTES_PER_SITE_PASS * 2 * sites / (ms_step / 1e3) / 1e9 / hbm
+        roofline["hbm_peak_gbs"] = hbm
+    except (OSError, KeyError, ValueError):
+        pass
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian + splitmix64 phase noise)",
+            "config": config_dict(c), "roofline": roofline, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "clocks": clocks.summary(), "wall_s_timed_loop": wall,
+        }
+    s.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+# ----------------------------------------------------------- CPU oracle ----
+def oracle_rate(p, nx, steps, seconds=None):
+    """Oracle site-steps/s on an nx x nx grid with the workload's dx, dt and physics."""
+    import oracle
+    from paper_2105_10517_gb300 import inputs
+    dx = p["xlen"] / p["nx"]
+    q = dict(p, nx=nx, ny=nx, xlen=dx * nx, ylen=dx * nx)
+    psi = inputs.gaussian_state(nx, nx, q["xlen"], q["ylen"], seed=2)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        psi = oracle.step(q, psi, oracle.IMAG)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (seconds is not None and el >= seconds and done >= 2):
+            break
+    return nx * nx * done / el, done, el
+
+
+def cpu_baseline(p, seconds):
+    rate, done, el = oracle_rate(p, p["nx"], None, seconds)
+    return {"value": rate / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} imaginary-time steps of the full {p['nx']}x{p['ny']} workload "
+                      f"({el:.1f} s, single-threaded C oracle)"}
+
+
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return None
+    import oracle
+    oracle.build()
+    c, p = workload()
+    # calibrate: size the sample grid so that warmup + steps take about two minutes
+    r, _, _ = oracle_rate(p, 64, 3)
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n = int(max(16, min(p["nx"], math.sqrt(budget * r))))
+    oracle_rate(p, n, max(1, args.warmup))
+    rate, done, el = oracle_rate(p, n, args.steps)
+    value = rate / 1e6
+    sample = (f"{n}x{n} grid with the {p['nx']}x{p['ny']} workload's dx, dt and physics, "
+              f"{done} timed steps after {args.warmup} warm-up steps ({el:.1f} s)")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian)", "config": config_dict(c),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out:
+            print(json.dumps(out))
+        return
+    out = run_ours(args)
+    if out is not None:
+        world = out["n_gpus"]
+        if world == 1 and not args.no_cpu_baseline:
+            _, p = workload()
+            out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -47,6 +47,7 @@ struct gp_handle {
     double* obs_out = nullptr; // [8]
     int* flag = nullptr;       // bit0 coefficient convergence, bit1 norm, bit2 observables
     CoefSet coef[2];           // per mode
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // gp_profile_step
     bool scale_pending = false;
     long long steps = 0;
 };
@@ -310,6 +311,8 @@ void gp_destroy(gp_handle* h)
     cudaFree(h->scal);
     cudaFree(h->obs_out);
     cudaFree(h->flag);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -395,6 +398,37 @@ int gp_propagate(gp_handle* h, long long nsteps, int mode)
     }
     h->steps += nsteps;
     return sync_status(h);
+}
+
+int gp_profile_step(gp_handle* h, int mode, float* ms_out)
+{
+    if (!h || !ms_out || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
+    int st = ensure_coef(h, mode);
+    if (st) return st;
+    const CoefSet& cs = h->coef[mode];
+    if (mode == GP_REAL && (st = flush_scale(h))) return st;
+    for (auto& e : h->ev)
+        if (!e) CK(cudaEventCreate(&e));
+    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+    int gy = (cs.ty.nlines + cs.ty.R - 1) / cs.ty.R;
+    if (mode == GP_IMAG) ay.partials = h->partials;
+    CK(cudaEventRecord(h->ev[0], h->stream));
+    LK(launch_xpass(ax, mode, h->stream));
+    CK(cudaEventRecord(h->ev[1], h->stream));
+    LK(launch_ypass(ay, mode, h->stream));
+    CK(cudaEventRecord(h->ev[2], h->stream));
+    if (mode == GP_IMAG) {
+        LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
+        h->scale_pending = true;
+    }
+    CK(cudaEventRecord(h->ev[3], h->stream));
+    CK(cudaEventSynchronize(h->ev[3]));
+    CK(cudaEventElapsedTime(&ms_out[0], h->ev[0], h->ev[1]));
+    CK(cudaEventElapsedTime(&ms_out[1], h->ev[1], h->ev[2]));
+    CK(cudaEventElapsedTime(&ms_out[2], h->ev[2], h->ev[3]));
+    CK(cudaEventElapsedTime(&ms_out[3], h->ev[0], h->ev[3]));
+    h->steps += 1;
+    return GP_OK;
 }
 
 int gp_apply_substep(gp_handle* h, int which, int mode)

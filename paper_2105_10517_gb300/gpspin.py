@@ -32,7 +32,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-           "gp_propagate", "gp_observables", "gp_apply_substep", "gp_strerror"]
+           "gp_propagate", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_strerror"]
 
 
 def _nvcc():
@@ -124,10 +124,11 @@ def load():
     lib.gp_propagate.argtypes = [vp, ctypes.c_longlong, ip]
     lib.gp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
     lib.gp_apply_substep.argtypes = [vp, ip, ip]
+    lib.gp_profile_step.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_float)]
     lib.gp_strerror.argtypes = [ip]
     lib.gp_strerror.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-                 "gp_propagate", "gp_observables", "gp_apply_substep"):
+                 "gp_propagate", "gp_observables", "gp_apply_substep", "gp_profile_step"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -196,16 +197,32 @@ class Solver:
         self.params = dict(params)
         self._p = p
 
-    def set_state(self, psi, normalize=False):
-        a = np.ascontiguousarray(psi, dtype=np.complex128)
+    def _host_ptr(self, buf, what):
+        """Pointer to a host complex128 buffer of shape (3, ny, nx): a numpy array
+        or a (pinned) torch CPU tensor."""
+        if hasattr(buf, "data_ptr"):
+            if tuple(buf.shape) != (3, self.ny, self.nx) or not buf.is_contiguous() or buf.is_cuda:
+                raise ValueError(f"{what}: need a contiguous CPU tensor of shape (3, {self.ny}, {self.nx})")
+            if str(buf.dtype) != "torch.complex128":
+                raise ValueError(f"{what}: need complex128")
+            return ctypes.cast(ctypes.c_void_p(buf.data_ptr()), ctypes.POINTER(ctypes.c_double)), buf
+        a = np.ascontiguousarray(buf, dtype=np.complex128)
         if a.shape != (3, self.ny, self.nx):
-            raise ValueError(f"psi must have shape (3, {self.ny}, {self.nx})")
-        _check(load().gp_set_state(self._h, _dptr(a), int(bool(normalize))), "gp_set_state")
+            raise ValueError(f"{what}: psi must have shape (3, {self.ny}, {self.nx})")
+        return _dptr(a), a
+
+    def set_state(self, psi, normalize=False):
+        ptr, keep = self._host_ptr(psi, "set_state")
+        _check(load().gp_set_state(self._h, ptr, int(bool(normalize))), "gp_set_state")
 
     def get_state(self, out=None):
         if out is None:
             out = np.empty((3, self.ny, self.nx), dtype=np.complex128)
-        _check(load().gp_get_state(self._h, _dptr(out)), "gp_get_state")
+        elif not hasattr(out, "data_ptr") and (not isinstance(out, np.ndarray) or out.dtype != np.complex128
+                                               or not out.flags.c_contiguous):
+            raise ValueError("get_state: out must be a C-contiguous complex128 array")
+        ptr, keep = self._host_ptr(out, "get_state")
+        _check(load().gp_get_state(self._h, ptr), "gp_get_state")
         return out
 
     def init_gaussian(self, frac=(0.25, 0.5, 0.25), seed=1, phase_noise=1e-3):
@@ -218,6 +235,12 @@ class Solver:
     def apply_substep(self, which, mode=IMAG):
         w = {"P": SUB_P, "X": SUB_X, "Y": SUB_Y}.get(which, which)
         _check(load().gp_apply_substep(self._h, int(w), int(mode)), "gp_apply_substep")
+
+    def profile_step(self, mode=IMAG):
+        """One step with per-kernel device times (ms): x-pass, y-pass, normalisation, whole step."""
+        ms = (ctypes.c_float * 4)()
+        _check(load().gp_profile_step(self._h, int(mode), ms), "gp_profile_step")
+        return list(ms)
 
     def observables(self):
         o = Obs()
