@@ -32,7 +32,8 @@ typedef enum {
     GP_ERR_OOM = 2,       /* device allocation failed                                     */
     GP_ERR_CUDA = 3,      /* a CUDA runtime call failed; the handle should be destroyed   */
     GP_ERR_NONFINITE = 4, /* a reduction met NaN/Inf in psi; the state is kept as is      */
-    GP_ERR_UNSUPPORTED = 5/* parameters outside what the tabulated solver supports        */
+    GP_ERR_UNSUPPORTED = 5,/* parameters outside what the tabulated solver supports       */
+    GP_ERR_TOO_LARGE = 6  /* grid larger than the fixed scratch of gp_propagate_noalloc    */
 } gp_status;
 
 typedef enum { GP_IMAG = 0, GP_REAL = 1 } gp_mode;
@@ -127,6 +128,26 @@ int gp_apply_substep(gp_handle* h, int which, int mode);
  * partial norms), ms_out[2] (normalisation, 0 in real time) and ms_out[3]
  * (the whole step, first event to last).  ms_out must hold 4 floats. */
 int gp_profile_step(gp_handle* h, int mode, float* ms_out);
+
+/* No-allocation variant of gp_propagate (the paper has no counterpart: it
+ * exists for callers that must not allocate device memory -- e.g. a plugin
+ * whose host application owns the GPU memory pool, or a real-time loop under a
+ * no-allocation rule -- and therefore cannot create a gp_handle).
+ *   params  problem statement as for gp_create; nx and ny must be <= 256
+ *           (otherwise GP_ERR_TOO_LARGE, before any device work).
+ *   psi_dev DEVICE pointer owned by the caller: psi[3][ny][nx] complex128,
+ *           advanced in place by nsteps steps in mode GP_IMAG or GP_REAL;
+ *           in imaginary time it is returned normalised to 1.
+ *   cuda_stream  a cudaStream_t (NULL: the legacy default stream).
+ * The call allocates nothing: its intermediate, coefficient tables, partial
+ * sums and scalars live in fixed device arrays of the library (about 8.6 MB,
+ * held on every device that loads the library until the process exits).  The
+ * first call on a device looks up their addresses (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls share these
+ * arrays: two calls whose device work overlaps (other streams, other host
+ * threads) race and corrupt each other's results.  Synchronous with respect to
+ * cuda_stream. */
+int gp_propagate_noalloc(const gp_params* params, double* psi_dev, long long nsteps, int mode, void* cuda_stream);
 
 /* Human-readable text for a gp_status. */
 const char* gp_strerror(int status);

@@ -52,9 +52,9 @@ struct gp_handle {
     long long steps = 0;
 };
 
-namespace {
+namespace gpspin {
 
-bool is_finite(double v) { return std::isfinite(v); }
+static bool is_finite(double v) { return std::isfinite(v); }
 
 int validate(const gp_params* p)
 {
@@ -133,6 +133,10 @@ int choose_tiling(int L, int nlines, double cpmax, LineTiling* t)
     t->smem = smem_of(R);
     return GP_OK;
 }
+
+}  // namespace gpspin
+
+namespace {
 
 #define CK(x)                                                  \
     do {                                                       \
@@ -254,6 +258,7 @@ const char* gp_strerror(int s)
     case GP_ERR_CUDA: return "CUDA runtime error";
     case GP_ERR_NONFINITE: return "non-finite values in the wave function";
     case GP_ERR_UNSUPPORTED: return "parameters outside the supported range of the tabulated line solver";
+    case GP_ERR_TOO_LARGE: return "grid larger than the fixed scratch of gp_propagate_noalloc (nx, ny <= 256)";
     default: return "unknown status";
     }
 }

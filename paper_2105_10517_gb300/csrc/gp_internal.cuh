@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "../../include/gpspin.h"
+
 namespace gpspin {
 
 // Head length of the tabulated Thomas factorisation and of the fixup powers.
@@ -77,6 +79,12 @@ struct PassArgs {
 
 namespace gpspin {
 int report_cuda(cudaError_t e, const char* what);
+// parameter checks and tiling (gp_capi.cu)
+int validate(const gp_params* p);
+int eta_of(const gp_params& p);
+double gamma_of(const gp_params& p);
+double max_cp(const gp_params& p, int dir, int mode);
+int choose_tiling(int L, int nlines, double cpmax, LineTiling* t);
 // launchers (gp_sweeps.cu)
 int launch_coef(LineCoef* coef, int nlines, int dir, int mode, double h, double line_len, double line_h,
                 double dt, double omeg, double gamma, int eta, int* status, cudaStream_t st);

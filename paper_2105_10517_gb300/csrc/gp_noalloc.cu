@@ -1,0 +1,158 @@
+// gp_noalloc.cu -- gp_propagate_noalloc: the time step of gp_propagate for
+// callers that must not allocate device memory.
+//
+// Who needs this: code that runs inside a host application which owns the
+// device memory budget (a plugin that gets its buffers from the host's pool,
+// a real-time loop with a no-allocation rule, a process sharing a GPU under a
+// fixed memory quota).  Such a caller already holds the wave function in device
+// memory but may not call cudaMalloc/cudaFree, so it cannot create a gp_handle.
+//
+// Everything the step needs besides the caller's psi -- the transposed
+// intermediate between the two line passes, the Thomas coefficient tables, the
+// trap factors, the per-CTA partial norms, the normalisation scalar and a status
+// flag -- lives in the file-scope __device__ arrays below.  Their size is fixed
+// for grids up to kMaxLine x kMaxLine points (about 8.6 MB); every GPU that loads
+// the library keeps them until the process exits.
+#include "gp_internal.cuh"
+
+#include <mutex>
+
+namespace gpspin {
+namespace {
+
+constexpr int kMaxLine = 256;                       // nx, ny <= 256
+constexpr size_t kMaxSites = (size_t)kMaxLine * kMaxLine;
+
+static __device__ __align__(256) double2 g_work[3 * kMaxSites];
+static __device__ __align__(256) LineCoef g_coef_x[3 * kMaxLine];
+static __device__ __align__(256) LineCoef g_coef_y[3 * kMaxLine];
+static __device__ __align__(256) double2 g_ex[kMaxLine];
+static __device__ __align__(256) double2 g_ey[kMaxLine];
+static __device__ __align__(256) double g_partials[kMaxLine];
+static __device__ __align__(256) double g_scale[2];
+static __device__ __align__(256) int g_flag;
+
+// Device addresses of the arrays above.  In host code the array names are
+// host-side stand-ins, not device addresses, so each device looks them up once
+// with cudaGetSymbolAddress while it is current.
+struct Scratch {
+    double2* work;
+    LineCoef* cx;
+    LineCoef* cy;
+    double2* ex;
+    double2* ey;
+    double* partials;
+    double* scale;
+    int* flag;
+};
+
+constexpr int kMaxDevices = 64;
+std::once_flag g_once[kMaxDevices];
+Scratch g_scratch[kMaxDevices];
+int g_setup_status[kMaxDevices];
+
+int lookup(void** p, const void* sym, const char* what)
+{
+    return report_cuda(cudaGetSymbolAddress(p, sym), what);
+}
+
+void setup(int dev)
+{
+    Scratch s{};
+    int bad = 0;
+    bad |= lookup((void**)&s.work, g_work, "cudaGetSymbolAddress(g_work)");
+    bad |= lookup((void**)&s.cx, g_coef_x, "cudaGetSymbolAddress(g_coef_x)");
+    bad |= lookup((void**)&s.cy, g_coef_y, "cudaGetSymbolAddress(g_coef_y)");
+    bad |= lookup((void**)&s.ex, g_ex, "cudaGetSymbolAddress(g_ex)");
+    bad |= lookup((void**)&s.ey, g_ey, "cudaGetSymbolAddress(g_ey)");
+    bad |= lookup((void**)&s.partials, g_partials, "cudaGetSymbolAddress(g_partials)");
+    bad |= lookup((void**)&s.scale, g_scale, "cudaGetSymbolAddress(g_scale)");
+    bad |= lookup((void**)&s.flag, &g_flag, "cudaGetSymbolAddress(g_flag)");
+    g_scratch[dev] = s;
+    g_setup_status[dev] = bad ? GP_ERR_CUDA : GP_OK;
+}
+
+#define NK(x)                                                  \
+    do {                                                       \
+        if (report_cuda((x), #x) != 0) return GP_ERR_CUDA;     \
+    } while (0)
+#define NL(x)                                                  \
+    do {                                                       \
+        if ((x) != 0) return GP_ERR_CUDA;                      \
+    } while (0)
+
+}  // namespace
+}  // namespace gpspin
+
+using namespace gpspin;
+
+extern "C" int gp_propagate_noalloc(const gp_params* params, double* psi_dev, long long nsteps, int mode,
+                                    void* cuda_stream)
+{
+    int st = validate(params);
+    if (st) return st;
+    if (!psi_dev || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
+    const gp_params& p = *params;
+    if (p.nx > kMaxLine || p.ny > kMaxLine) return GP_ERR_TOO_LARGE;
+    if (nsteps == 0) return GP_OK;
+    int dev = 0;
+    NK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return GP_ERR_CUDA;
+    std::call_once(g_once[dev], setup, dev);
+    if (g_setup_status[dev] != GP_OK) return g_setup_status[dev];
+    const Scratch& S = g_scratch[dev];
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+
+    LineTiling tx, ty;
+    if ((st = choose_tiling(p.nx, p.ny, max_cp(p, 0, mode), &tx))) return st;
+    if ((st = choose_tiling(p.ny, p.nx, max_cp(p, 1, mode), &ty))) return st;
+
+    // The arrays keep the previous call's contents: the flag must start at zero
+    // and the scale at one; every other array is fully rewritten below.
+    const double dx = p.xlen / p.nx, dy = p.ylen / p.ny;
+    NK(cudaMemsetAsync(S.flag, 0, sizeof(int), stream));
+    NL(launch_set_scalar(S.scale, 1.0, stream));
+    NL(launch_coef(S.cx, p.ny, 0, mode, dx, p.ylen, dy, p.dt, p.omeg, gamma_of(p), eta_of(p), S.flag, stream));
+    NL(launch_coef(S.cy, p.nx, 1, mode, dy, p.xlen, dx, p.dt, p.omeg, gamma_of(p), eta_of(p), S.flag, stream));
+    NL(launch_trap_table(S.ex, p.nx, p.xlen, p.wx, p.dt, mode, stream));
+    NL(launch_trap_table(S.ey, p.ny, p.ylen, p.wy, p.dt, mode, stream));
+    int flag = 0;
+    NK(cudaMemcpyAsync(&flag, S.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    NK(cudaStreamSynchronize(stream));
+    if (flag & 1) return GP_ERR_UNSUPPORTED;
+
+    PassArgs ax{}, ay{};
+    ax.nx = ay.nx = p.nx;
+    ax.ny = ay.ny = p.ny;
+    ax.scale = ay.scale = S.scale;
+    ax.dt = ay.dt = p.dt;
+    ax.c0 = ay.c0 = p.c0;
+    ax.c2 = ay.c2 = p.c2;
+    ax.rabi = ay.rabi = p.rabi;
+    ax.ex = ay.ex = S.ex;
+    ax.ey = ay.ey = S.ey;
+    ax.do_p = ay.do_p = 1;
+    ax.do_solve = ay.do_solve = 1;
+    ax.in = reinterpret_cast<const double2*>(psi_dev);
+    ax.out = S.work;
+    ax.coef = S.cx;
+    ax.t = tx;
+    ay.in = S.work;
+    ay.out = reinterpret_cast<double2*>(psi_dev);
+    ay.coef = S.cy;
+    ay.t = ty;
+    const double da = dx * dy;
+    const int gy = (ty.nlines + ty.R - 1) / ty.R;
+    if (mode == GP_IMAG) ay.partials = S.partials;
+    for (long long s = 0; s < nsteps; ++s) {
+        NL(launch_xpass(ax, mode, stream));
+        NL(launch_ypass(ay, mode, stream));
+        if (mode == GP_IMAG) NL(launch_finalize_norm(S.partials, gy, da, S.scale, S.flag, stream));
+    }
+    // leave the caller's psi normalised (imaginary time) and the scale at one
+    if (mode == GP_IMAG) NL(launch_apply_scale(reinterpret_cast<double2*>(psi_dev), 3 * (size_t)p.nx * p.ny,
+                                               S.scale, stream));
+    NK(cudaMemcpyAsync(&flag, S.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    NK(cudaStreamSynchronize(stream));
+    return (flag & 2) ? GP_ERR_NONFINITE : GP_OK;
+}

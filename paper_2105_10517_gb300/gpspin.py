@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB_PATH = os.path.join(PKG, "libgpspin.so")
 BUILD_DIR = os.path.join(PKG, "_build")
-SOURCES = ["gp_capi.cu", "gp_sweeps.cu", "gp_reduce.cu"]
+SOURCES = ["gp_capi.cu", "gp_sweeps.cu", "gp_reduce.cu", "gp_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
 
@@ -28,11 +28,12 @@ FP64 = 0
 SUB_P, SUB_X, SUB_Y = 0, 1, 2
 
 STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP_ERR_NONFINITE",
-          5: "GP_ERR_UNSUPPORTED"}
+          5: "GP_ERR_UNSUPPORTED", 6: "GP_ERR_TOO_LARGE"}
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-           "gp_propagate", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_strerror"]
+           "gp_propagate", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_propagate_noalloc",
+           "gp_strerror"]
 
 
 def _nvcc():
@@ -125,6 +126,8 @@ def load():
     lib.gp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
     lib.gp_apply_substep.argtypes = [vp, ip, ip]
     lib.gp_profile_step.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_float)]
+    lib.gp_propagate_noalloc.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_longlong, ip, vp]
+    lib.gp_propagate_noalloc.restype = ctypes.c_int
     lib.gp_strerror.argtypes = [ip]
     lib.gp_strerror.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
@@ -159,6 +162,15 @@ def make_params(p):
 
 def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def propagate_noalloc(params, psi_dev_ptr, nsteps, mode=IMAG, stream=None):
+    """gp_propagate_noalloc on a caller-owned device buffer (an integer device
+    address of psi[3][ny][nx] complex128, e.g. a torch tensor's data_ptr())."""
+    p = make_params(params)
+    s = ctypes.c_void_p(int(stream)) if stream is not None else None
+    _check(load().gp_propagate_noalloc(ctypes.byref(p), ctypes.c_void_p(int(psi_dev_ptr)), int(nsteps), int(mode), s),
+           "gp_propagate_noalloc")
 
 
 class Solver:
