@@ -47,7 +47,7 @@ INST_PER_SITE = {"xpass": 177, "ypass": 63}
 BYTES_PER_SITE_PASS = 96
 # DRAM traffic of one launch from an ncu capture (profiles/), keyed by kernel
 # and valid only while the kernel source is unchanged (sha256 prefix).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"xpass_kernel<0> vortex512": (16195584 + 0, "9b9e02dd3793dbcc")}  # profiles/xpass_vortex512.md
 
 L2_FLUSH_BYTES = 256 << 20
 
