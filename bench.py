@@ -89,6 +89,23 @@ def config_dict(c):
     }
 
 
+# ----------------------------------------------------------- rank logic ----
+def max_over_ranks(x, dist, device):
+    """Max of a float over all ranks (the slowest rank sets the job's time)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, sites, steps, t_max_ms):
+    """Site-steps of all ranks (each advances its own replica) over the slowest
+    rank's time, in Msite-steps/s."""
+    return world * sites * steps / (t_max_ms / 1e3) / 1e6
+
+
 # --------------------------------------------------------------- clocks ----
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -196,12 +213,8 @@ def run_ours(args):
     ms_n = statistics.fmean(q[2] for q in per)
     ms_step = statistics.fmean(q[3] for q in per)
     total_ms = ms_step * args.steps
-    t_max = total_ms
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * sites * args.steps / (t_max / 1e3) / 1e6
+    t_max = max_over_ranks(total_ms, dist, "cuda")
+    value = whole_job_value(world, sites, args.steps, t_max)
 
     # end to end through the public API with pinned host buffers
     e2e = None
@@ -222,11 +235,7 @@ def run_ours(args):
             s.get_state(b)
             a, b = b, a
         barrier()
-        el = time.perf_counter() - te
-        if dist:
-            tt = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
+        el = max_over_ranks(time.perf_counter() - te, dist, "cuda")
         nbytes = 3 * sites * 16
         e2e = {"value": world * sites * args.e2e_steps / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps,
