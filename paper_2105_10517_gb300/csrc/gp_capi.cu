@@ -48,6 +48,7 @@ struct gp_handle {
     int* flag = nullptr;       // bit0 coefficient convergence, bit1 norm, bit2 observables
     CoefSet coef[2];           // per mode
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // gp_profile_step
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};               // kGraphSteps steps per mode
     bool scale_pending = false;
     long long steps = 0;
 };
@@ -147,6 +148,8 @@ namespace {
         if ((x) != 0) return GP_ERR_CUDA;       \
     } while (0)
 
+void drop_graphs(gp_handle* h);
+
 void free_coef(CoefSet& c)
 {
     cudaFree(c.cx);
@@ -175,6 +178,7 @@ int ensure_coef(gp_handle* h, int mode)
             return GP_ERR_OOM;
         }
     }
+    drop_graphs(h);
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     const double dx = p.xlen / p.nx, dy = p.ylen / p.ny;
     LK(launch_coef(cs.cx, p.ny, 0, mode, dx, p.ylen, dy, p.dt, p.omeg, gamma_of(p), eta_of(p), h->flag, h->stream));
@@ -243,6 +247,57 @@ int sync_status(gp_handle* h)
 {
     CK(cudaStreamSynchronize(h->stream));
     return GP_OK;
+}
+
+void drop_graphs(gp_handle* h)
+{
+    for (auto& g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Launch sequence of n steps (x-pass, y-pass and, in imaginary time, the
+// normalisation) on the handle's stream.
+int enqueue_steps(gp_handle* h, int mode, const PassArgs& ax, const PassArgs& ay, int gy, long long n)
+{
+    for (long long s = 0; s < n; ++s) {
+        LK(launch_xpass(ax, mode, h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
+        if (mode == GP_IMAG) LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
+    }
+    return GP_OK;
+}
+
+// Runs n steps: whole blocks of kGraphSteps steps replay one captured CUDA
+// graph (captured on first use, dropped when parameters or tables change); the
+// remainder is launched directly.  If capture is not possible on this stream the
+// steps are launched directly.
+constexpr int kGraphSteps = 16;
+
+int run_steps(gp_handle* h, int mode, const PassArgs& ax, const PassArgs& ay, int gy, long long n)
+{
+    if (n >= kGraphSteps && !h->graph[mode]) {
+        // one direct step first: it sets the kernels' shared-memory attributes
+        int st = enqueue_steps(h, mode, ax, ay, gy, 1);
+        if (st) return st;
+        --n;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            int cst = enqueue_steps(h, mode, ax, ay, gy, kGraphSteps);
+            cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+            if (cst == GP_OK && e == cudaSuccess && g) {
+                if (cudaGraphInstantiate(&h->graph[mode], g, 0) != cudaSuccess) h->graph[mode] = nullptr;
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();  // a failed capture only means direct launches
+    }
+    if (h->graph[mode]) {
+        for (; n >= kGraphSteps; n -= kGraphSteps) CK(cudaGraphLaunch(h->graph[mode], h->stream));
+    }
+    return enqueue_steps(h, mode, ax, ay, gy, n);
 }
 
 }  // namespace
@@ -318,6 +373,8 @@ void gp_destroy(gp_handle* h)
     cudaFree(h->flag);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
+    for (auto& g : h->graph)
+        if (g) cudaGraphExecDestroy(g);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -331,6 +388,7 @@ int gp_set_params(gp_handle* h, const gp_params* params)
         params->precision != h->p.precision)
         return GP_ERR_ARG;
     h->p = *params;
+    drop_graphs(h);  // the captured launches hold c0, c2, R and dt by value
     return GP_OK;
 }
 
@@ -384,23 +442,14 @@ int gp_propagate(gp_handle* h, long long nsteps, int mode)
     const CoefSet& cs = h->coef[mode];
     if (mode == GP_REAL && (st = flush_scale(h))) return st;
     PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+    int gy = (cs.ty.nlines + cs.ty.R - 1) / cs.ty.R;
+    if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
     if (mode == GP_IMAG) {
-        int gy = (cs.ty.nlines + cs.ty.R - 1) / cs.ty.R;
-        if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
         ay.partials = h->partials;
         CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
-        for (long long s = 0; s < nsteps; ++s) {
-            LK(launch_xpass(ax, mode, h->stream));
-            LK(launch_ypass(ay, mode, h->stream));
-            LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
-        }
-        h->scale_pending = true;
-    } else {
-        for (long long s = 0; s < nsteps; ++s) {
-            LK(launch_xpass(ax, mode, h->stream));
-            LK(launch_ypass(ay, mode, h->stream));
-        }
     }
+    if ((st = run_steps(h, mode, ax, ay, gy, nsteps))) return st;
+    if (mode == GP_IMAG) h->scale_pending = true;
     h->steps += nsteps;
     return sync_status(h);
 }

@@ -106,10 +106,12 @@ __global__ void trap_table_kernel(double2* out, int n, double len, double w, dou
 // Spin-1: (n.Sigma)^3 = n.Sigma, so with M = dt B.Sigma and u = dt^2 |B|^2
 //   imaginary: exp(-M) = I - s1(u) M + s2(u) M^2,  s1 = sinh(t)/t, s2 = (cosh t - 1)/t^2
 //   real:      exp(-iM) = I - i s1(u) M - s2(u) M^2, s1 = sin(t)/t,  s2 = (1 - cos t)/t^2
-// with t = sqrt(u); both are power series in u, used directly for u <= 1/100
-// (five terms reach 2.5e-18 relative).  The scalar factor exp(-tau' c0 rho) is a
-// Taylor series for dt c0 rho <= 1/8 (eleven terms, 3e-18); larger arguments
-// take the library exp / sincos.  The trap factor comes from the per-axis tables.
+// with t = sqrt(u); both are power series in u, used directly: three terms for
+// u <= 1e-4 and five for u <= 1/100 (first omitted term <= 2.5e-18 relative).
+// The scalar factor exp(-tau' c0 rho) is a Taylor series: eight terms for
+// dt c0 rho <= 1/64 (imaginary time) and eleven/twelve terms up to 1/8 (<= 3e-18);
+// larger arguments take the library exp / sincos.  The trap factor comes from
+// the per-axis tables.
 struct PConst {
     double dtc0;  // dt c0 s^2
     double dtc2;  // dt c2 s^2
@@ -145,9 +147,15 @@ __device__ __forceinline__ void pointwise(double2& a, double2& b, double2& c, do
     double bx = fma(k.dtc2, fr, k.dtr);
     double by = k.dtc2 * fi;
     double bz = k.dtc2 * (rp - rm);
-    double u = fma(2.0 * bx, bx, fma(2.0 * by, by, bz * bz));
+    double u = fma(2.0, fma(bx, bx, by * by), bz * bz);
     double s1, s2;
-    if (u <= 0.01) {
+    if (u <= 1e-4) {
+        // three terms: the first omitted term of s1 is u^3/7! <= 2e-16 and it multiplies
+        // M psi, |M psi| <= sqrt(u) |psi| <= 1e-2 |psi|, so psi' changes by <= 2e-18 |psi|
+        const double su = MODE == 1 ? -u : u;
+        s1 = fma(fma(su, 1.0 / 120.0, 1.0 / 6.0), su, 1.0);
+        s2 = fma(fma(su, 1.0 / 720.0, 1.0 / 24.0), su, 0.5);
+    } else if (u <= 0.01) {
         const double su = MODE == 1 ? -u : u;
         s1 = fma(fma(fma(fma(su, 1.0 / 362880.0, 1.0 / 5040.0), su, 1.0 / 120.0), su, 1.0 / 6.0), su, 1.0);
         s2 = fma(fma(fma(fma(su, 1.0 / 3628800.0, 1.0 / 40320.0), su, 1.0 / 720.0), su, 1.0 / 24.0), su, 0.5);
@@ -189,7 +197,12 @@ __device__ __forceinline__ void pointwise(double2& a, double2& b, double2& c, do
         c = cmul(ph, tc);
     } else {
         double e;
-        if (x <= 0.125) {
+        if (x <= 0.015625) {
+            // eight terms for x <= 1/64: the first omitted one is x^8/8! <= 1.7e-19
+            const double mx = -x;
+            e = fma(fma(fma(fma(fma(fma(fma(mx, 1.0 / 5040.0, 1.0 / 720.0), mx, 1.0 / 120.0), mx, 1.0 / 24.0), mx,
+                                1.0 / 6.0), mx, 0.5), mx, 1.0), mx, 1.0);
+        } else if (x <= 0.125) {
             const double mx = -x;
             e = fma(fma(fma(fma(fma(fma(fma(fma(fma(fma(mx, 1.0 / 39916800.0, 1.0 / 3628800.0), mx, 1.0 / 362880.0),
                                                     mx, 1.0 / 40320.0), mx, 1.0 / 5040.0), mx, 1.0 / 720.0),
@@ -335,7 +348,8 @@ __global__ void __launch_bounds__(512) xpass_kernel(PassArgs A)
         size_t o = (size_t)j * nx + i;
         double2 a = A.in[o], b = A.in[plane + o], c = A.in[2 * plane + o];
         if (A.do_p) {
-            double2 ev = cmul(A.ex[i], A.ey[j]);
+            // the trap factor is real in imaginary time
+            double2 ev = MODE == 1 ? cmul(A.ex[i], A.ey[j]) : make_double2(A.ex[i].x * A.ey[j].x, 0.0);
             pointwise<MODE>(a, b, c, ev, k);
         } else {
             a = make_double2(s * a.x, s * a.y);
