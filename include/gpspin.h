@@ -38,7 +38,12 @@ typedef enum {
 
 typedef enum { GP_IMAG = 0, GP_REAL = 1 } gp_mode;
 typedef enum { GP_SO_NONE = 0, GP_SO_RASHBA = 1, GP_SO_DRESSELHAUS = 2 } gp_so_type;
-typedef enum { GP_FP64 = 0 } gp_precision;
+/* GP_FP64: complex128 storage and arithmetic throughout.
+ * GP_FP32_MIXED: psi is stored and propagated as complex64 (FP32 sweeps and
+ * pointwise substep); the Thomas coefficient tables are computed in FP64, the
+ * norm and observable reductions run in FP64, and gp_refine_fp64 continues the
+ * propagation in FP64 (the precision form of the method's hot path). */
+typedef enum { GP_FP64 = 0, GP_FP32_MIXED = 1 } gp_precision;
 
 /* Problem statement (Eqs. S.1-S.4 and the input parameters of the program
  * summary): grid nx x ny on [-xlen/2, xlen/2) x [-ylen/2, ylen/2), time step dt,
@@ -110,6 +115,11 @@ int gp_init_gaussian(gp_handle* h, const double frac[3], unsigned long long seed
  * after every step.  mode GP_REAL propagates i d_t psi = H psi.  nsteps = 0 is
  * a no-op. */
 int gp_propagate(gp_handle* h, long long nsteps, int mode);
+
+/* Precision form: widens a GP_FP32_MIXED handle's complex64 state to complex128
+ * (exactly) and advances it by nsteps FP64 steps in the given mode; the handle
+ * propagates in FP64 from then on.  On a GP_FP64 handle it equals gp_propagate. */
+int gp_refine_fp64(gp_handle* h, long long nsteps, int mode);
 
 /* Computes the observables of the current state on the device (FP64, fixed
  * reduction order, so repeated calls give bitwise identical results).

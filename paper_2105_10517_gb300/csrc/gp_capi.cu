@@ -2,6 +2,12 @@
 // state, Thomas coefficient cache, tiling choice and the step sequence of the
 // split-step Crank-Nicolson method (arXiv 2105.10517, program summary "Solution
 // method"; Supplementary Material Eqs. S.1-S.6).
+//
+// A handle created with precision GP_FP32_MIXED propagates a complex64 copy of
+// psi (float2 storage and sweeps; coefficient tables computed in FP64, norms
+// summed in FP64) until gp_refine_fp64 widens it to complex128 and continues in
+// FP64.  State input/output and observables always go through the complex128
+// buffer (widening float -> double is exact).
 #include "../../include/gpspin.h"
 #include "gp_internal.cuh"
 
@@ -16,14 +22,19 @@ namespace {
 
 constexpr int kNormBlocksMax = 4096;
 
+// Coefficient tables and tilings of one mode (imaginary or real time).
 struct CoefSet {
     bool valid = false;
     gp_params key{};
-    LineCoef* cx = nullptr;  // [ny][3] x-pass lines (rows)
-    LineCoef* cy = nullptr;  // [nx][3] y-pass lines (columns)
-    double2* ex = nullptr;   // [nx]
-    double2* ey = nullptr;   // [ny]
-    LineTiling tx{}, ty{};
+    LineCoef* cx = nullptr;   // [ny][3] x-pass lines (rows), FP64
+    LineCoef* cy = nullptr;   // [nx][3] y-pass lines (columns), FP64
+    double2* ex = nullptr;    // [nx]
+    double2* ey = nullptr;    // [ny]
+    LineCoefF* fx = nullptr;  // complex64 copies (FP32-storage handles only)
+    LineCoefF* fy = nullptr;
+    float2* fex = nullptr;
+    float2* fey = nullptr;
+    LineTiling tx{}, ty{}, ftx{}, fty{};
 };
 
 bool same_physics(const gp_params& a, const gp_params& b)
@@ -39,16 +50,19 @@ struct gp_handle {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
-    double2* psi = nullptr;    // [3][ny][nx]
+    int active = GP_FP64;      // precision of the propagated copy
+    double2* psi = nullptr;    // [3][ny][nx] complex128 state (authoritative when active == GP_FP64)
     double2* work = nullptr;   // [3][nx][ny] transposed intermediate / staging
+    float2* psi32 = nullptr;   // complex64 state (authoritative when active == GP_FP32_MIXED)
+    float2* work32 = nullptr;
     double* partials = nullptr;
     double* obs_part = nullptr;
-    double* scal = nullptr;    // [0] pending normalisation, [1] last norm
+    double* scal = nullptr;    // [0] pending normalisation, [1] last norm, [2] the constant 1
     double* obs_out = nullptr; // [8]
     int* flag = nullptr;       // bit0 coefficient convergence, bit1 norm, bit2 observables
     CoefSet coef[2];           // per mode
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // gp_profile_step
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};               // kGraphSteps steps per mode
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [precision][mode]
     bool scale_pending = false;
     long long steps = 0;
 };
@@ -61,13 +75,14 @@ int validate(const gp_params* p)
 {
     if (!p) return GP_ERR_ARG;
     if (p->nx < 4 || p->ny < 4) return GP_ERR_ARG;
-    if (!(p->xlen > 0) || !(p->ylen > 0) || !(p->dt > 0) || !is_finite(p->xlen) || !is_finite(p->ylen) || !is_finite(p->dt))
+    if (!(p->xlen > 0) || !(p->ylen > 0) || !(p->dt > 0) || !is_finite(p->xlen) || !is_finite(p->ylen) ||
+        !is_finite(p->dt))
         return GP_ERR_ARG;
     const double v[] = {p->wx, p->wy, p->c0, p->c2, p->omeg, p->gamma, p->rabi};
     for (double x : v)
         if (!is_finite(x)) return GP_ERR_ARG;
     if (p->so_type < 0 || p->so_type > 2) return GP_ERR_ARG;
-    if (p->precision != GP_FP64) return GP_ERR_ARG;
+    if (p->precision != GP_FP64 && p->precision != GP_FP32_MIXED) return GP_ERR_ARG;
     return GP_OK;
 }
 
@@ -77,7 +92,7 @@ double gamma_of(const gp_params& p) { return p.so_type == GP_SO_NONE ? 0.0 : p.g
 // Largest |c'_inf| over the lines and channels of one direction: the modulus of
 // the smaller root of alpha z^2 - beta z + gamma' = 0 (the fixed point of the
 // Thomas recurrence c'_k = gamma' / (beta - alpha c'_{k-1})).  It fixes how many
-// elements a chunk carry influences above FP64 rounding.
+// elements a chunk carry influences above rounding.
 double max_cp(const gp_params& p, int dir, int mode)
 {
     typedef std::complex<double> cd;
@@ -102,12 +117,18 @@ double max_cp(const gp_params& p, int dir, int mode)
     return best;
 }
 
-// Chunk length m, fixup length F and lines per CTA for lines of length L.
-int choose_tiling(int L, int nlines, double cpmax, LineTiling* t)
+// Chunk length m, fixup length F and lines per CTA for lines of length L:
+// F makes |c'_inf|^F <= 2^-60 (complex128) or 2^-26 (complex64); m >= H + F
+// with H the rows until the factorisation has converged (contraction |c'|^2
+// per row); R lines per CTA within ~100 KB of shared memory (two CTAs per SM)
+// and 512 threads.
+int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32)
 {
     if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
-    int F = cpmax > 0 ? (int)std::ceil(60.0 * std::log(2.0) / -std::log(cpmax)) + 1 : 1;
-    int H = (F + 1) / 2 + 2;  // rows until c'_k reaches c'_inf to 2^-60 (contraction |c'|^2 per row)
+    const double bits = fp32 ? 26.0 : 60.0;
+    const size_t elem = fp32 ? sizeof(float2) : sizeof(double2);
+    int F = cpmax > 0 ? (int)std::ceil(bits * std::log(2.0) / -std::log(cpmax)) + 1 : 1;
+    int H = (F + 1) / 2 + 2;
     if (F > kFix || H > kHead) return GP_ERR_UNSUPPORTED;
     int m = std::max(16, H + F);
     m = (m + 3) / 4 * 4;
@@ -117,8 +138,9 @@ int choose_tiling(int L, int nlines, double cpmax, LineTiling* t)
         Q = (L + m - 1) / m;
     }
     int Lp = Q * (m + 1) + 1;
-    auto smem_of = [&](int R) { return (size_t)(2 * 3 * R * Lp + 2 * 3 * R * Q) * sizeof(double2); };
+    auto smem_of = [&](int R) { return (size_t)(2 * 3 * R * Lp + 2 * 3 * R * Q) * elem; };
     int R = std::max(1, 256 / (3 * Q));
+    if (fp32) R = std::max(R, 4);  // >= 32-byte segments in the transposed store
     while (R > 1 && (smem_of(R) > 100 * 1024 || 3 * R * Q > 512)) --R;
     R = std::min(R, nlines);
     if (smem_of(R) > 227 * 1024) return GP_ERR_UNSUPPORTED;
@@ -143,12 +165,20 @@ namespace {
     do {                                                       \
         if (report_cuda((x), #x) != 0) return GP_ERR_CUDA;     \
     } while (0)
-#define LK(x)                                   \
-    do {                                        \
-        if ((x) != 0) return GP_ERR_CUDA;       \
+#define LK(x)                                                  \
+    do {                                                       \
+        if ((x) != 0) return GP_ERR_CUDA;                      \
     } while (0)
 
-void drop_graphs(gp_handle* h);
+void drop_graphs(gp_handle* h)
+{
+    for (auto& row : h->graph)
+        for (auto& g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+}
 
 void free_coef(CoefSet& c)
 {
@@ -156,24 +186,41 @@ void free_coef(CoefSet& c)
     cudaFree(c.cy);
     cudaFree(c.ex);
     cudaFree(c.ey);
+    cudaFree(c.fx);
+    cudaFree(c.fy);
+    cudaFree(c.fex);
+    cudaFree(c.fey);
     c = CoefSet{};
 }
+
+bool wants_fp32(const gp_handle* h) { return h->p.precision == GP_FP32_MIXED; }
 
 int ensure_coef(gp_handle* h, int mode)
 {
     CoefSet& cs = h->coef[mode];
     if (cs.valid && same_physics(cs.key, h->p)) return GP_OK;
     const gp_params& p = h->p;
-    LineTiling tx, ty;
-    int st = choose_tiling(p.nx, p.ny, max_cp(p, 0, mode), &tx);
+    const bool f32 = wants_fp32(h);
+    LineTiling tx, ty, ftx{}, fty{};
+    const double cx = max_cp(p, 0, mode), cy = max_cp(p, 1, mode);
+    int st = choose_tiling(p.nx, p.ny, cx, &tx);
     if (st) return st;
-    st = choose_tiling(p.ny, p.nx, max_cp(p, 1, mode), &ty);
-    if (st) return st;
+    if ((st = choose_tiling(p.ny, p.nx, cy, &ty))) return st;
+    if (f32) {
+        if ((st = choose_tiling(p.nx, p.ny, cx, &ftx, 1))) return st;
+        if ((st = choose_tiling(p.ny, p.nx, cy, &fty, 1))) return st;
+    }
     if (!cs.cx) {
-        if (cudaMalloc(&cs.cx, sizeof(LineCoef) * 3 * (size_t)p.ny) != cudaSuccess ||
-            cudaMalloc(&cs.cy, sizeof(LineCoef) * 3 * (size_t)p.nx) != cudaSuccess ||
-            cudaMalloc(&cs.ex, sizeof(double2) * p.nx) != cudaSuccess ||
-            cudaMalloc(&cs.ey, sizeof(double2) * p.ny) != cudaSuccess) {
+        bool ok = cudaMalloc(&cs.cx, sizeof(LineCoef) * 3 * (size_t)p.ny) == cudaSuccess &&
+                  cudaMalloc(&cs.cy, sizeof(LineCoef) * 3 * (size_t)p.nx) == cudaSuccess &&
+                  cudaMalloc(&cs.ex, sizeof(double2) * p.nx) == cudaSuccess &&
+                  cudaMalloc(&cs.ey, sizeof(double2) * p.ny) == cudaSuccess;
+        if (ok && f32)
+            ok = cudaMalloc(&cs.fx, sizeof(LineCoefF) * 3 * (size_t)p.ny) == cudaSuccess &&
+                 cudaMalloc(&cs.fy, sizeof(LineCoefF) * 3 * (size_t)p.nx) == cudaSuccess &&
+                 cudaMalloc(&cs.fex, sizeof(float2) * p.nx) == cudaSuccess &&
+                 cudaMalloc(&cs.fey, sizeof(float2) * p.ny) == cudaSuccess;
+        if (!ok) {
             free_coef(cs);
             return GP_ERR_OOM;
         }
@@ -181,24 +228,34 @@ int ensure_coef(gp_handle* h, int mode)
     drop_graphs(h);
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     const double dx = p.xlen / p.nx, dy = p.ylen / p.ny;
-    LK(launch_coef(cs.cx, p.ny, 0, mode, dx, p.ylen, dy, p.dt, p.omeg, gamma_of(p), eta_of(p), h->flag, h->stream));
-    LK(launch_coef(cs.cy, p.nx, 1, mode, dy, p.xlen, dx, p.dt, p.omeg, gamma_of(p), eta_of(p), h->flag, h->stream));
+    const double g = gamma_of(p);
+    const int eta = eta_of(p);
+    LK(launch_coef(cs.cx, p.ny, 0, mode, dx, p.ylen, dy, p.dt, p.omeg, g, eta, h->flag, h->stream));
+    LK(launch_coef(cs.cy, p.nx, 1, mode, dy, p.xlen, dx, p.dt, p.omeg, g, eta, h->flag, h->stream));
     LK(launch_trap_table(cs.ex, p.nx, p.xlen, p.wx, p.dt, mode, h->stream));
     LK(launch_trap_table(cs.ey, p.ny, p.ylen, p.wy, p.dt, mode, h->stream));
+    if (f32) {
+        LK(launch_coef(cs.fx, p.ny, 0, mode, dx, p.ylen, dy, p.dt, p.omeg, g, eta, h->flag, h->stream));
+        LK(launch_coef(cs.fy, p.nx, 1, mode, dy, p.xlen, dx, p.dt, p.omeg, g, eta, h->flag, h->stream));
+        LK(launch_trap_table(cs.fex, p.nx, p.xlen, p.wx, p.dt, mode, h->stream));
+        LK(launch_trap_table(cs.fey, p.ny, p.ylen, p.wy, p.dt, mode, h->stream));
+    }
     int flag = 0;
     CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     if (flag & 1) return GP_ERR_UNSUPPORTED;
     cs.tx = tx;
     cs.ty = ty;
+    cs.ftx = ftx;
+    cs.fty = fty;
     cs.key = p;
     cs.valid = true;
     return GP_OK;
 }
 
-PassArgs pass_args(gp_handle* h, const CoefSet& cs, int dir)
+template <typename C>
+void fill_common(gp_handle* h, PassArgsT<C>& a)
 {
-    PassArgs a{};
     a.nx = h->p.nx;
     a.ny = h->p.ny;
     a.scale = h->scal;
@@ -206,10 +263,16 @@ PassArgs pass_args(gp_handle* h, const CoefSet& cs, int dir)
     a.c0 = h->p.c0;
     a.c2 = h->p.c2;
     a.rabi = h->p.rabi;
-    a.ex = cs.ex;
-    a.ey = cs.ey;
     a.do_p = 1;
     a.do_solve = 1;
+}
+
+PassArgs pass_args(gp_handle* h, const CoefSet& cs, int dir)
+{
+    PassArgs a{};
+    fill_common(h, a);
+    a.ex = cs.ex;
+    a.ey = cs.ey;
     if (dir == 0) {
         a.in = h->psi;
         a.out = h->work;
@@ -224,6 +287,26 @@ PassArgs pass_args(gp_handle* h, const CoefSet& cs, int dir)
     return a;
 }
 
+PassArgsF pass_args_f32(gp_handle* h, const CoefSet& cs, int dir)
+{
+    PassArgsF a{};
+    fill_common(h, a);
+    a.ex = cs.fex;
+    a.ey = cs.fey;
+    if (dir == 0) {
+        a.in = h->psi32;
+        a.out = h->work32;
+        a.coef = cs.fx;
+        a.t = cs.ftx;
+    } else {
+        a.in = h->work32;
+        a.out = h->psi32;
+        a.coef = cs.fy;
+        a.t = cs.fty;
+    }
+    return a;
+}
+
 size_t n_elems(const gp_handle* h) { return 3 * (size_t)h->p.nx * h->p.ny; }
 double cell(const gp_handle* h) { return (h->p.xlen / h->p.nx) * (h->p.ylen / h->p.ny); }
 
@@ -234,12 +317,33 @@ int norm_blocks(const gp_handle* h)
     return (int)std::min<size_t>(std::max<size_t>(b, 1), 608);
 }
 
-// Makes the stored state the true state (no pending normalisation).
+// Makes the stored (active) state the true state (no pending normalisation).
 int flush_scale(gp_handle* h)
 {
     if (!h->scale_pending) return GP_OK;
-    LK(launch_apply_scale(h->psi, n_elems(h), h->scal, h->stream));
+    if (h->active == GP_FP32_MIXED) {
+        LK(launch_apply_scale(h->psi32, n_elems(h), h->scal, h->stream));
+    } else {
+        LK(launch_apply_scale(h->psi, n_elems(h), h->scal, h->stream));
+    }
     h->scale_pending = false;
+    return GP_OK;
+}
+
+// The complex128 buffer psi mirrors the complex64 state (exact widening); the
+// pending scale stays pending.
+int widen_into_psi(gp_handle* h)
+{
+    if (h->active != GP_FP32_MIXED) return GP_OK;
+    LK(launch_scaled_copy(h->psi, h->psi32, n_elems(h), h->scal + 2, h->stream));
+    return GP_OK;
+}
+
+// After psi (complex128) was written from outside: refresh the complex64 copy.
+int narrow_from_psi(gp_handle* h)
+{
+    if (h->active != GP_FP32_MIXED) return GP_OK;
+    LK(launch_narrow(h->psi32, h->psi, n_elems(h), h->stream));
     return GP_OK;
 }
 
@@ -249,18 +353,12 @@ int sync_status(gp_handle* h)
     return GP_OK;
 }
 
-void drop_graphs(gp_handle* h)
-{
-    for (auto& g : h->graph)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
-}
+int y_blocks(const LineTiling& t) { return (t.nlines + t.R - 1) / t.R; }
 
 // Launch sequence of n steps (x-pass, y-pass and, in imaginary time, the
 // normalisation) on the handle's stream.
-int enqueue_steps(gp_handle* h, int mode, const PassArgs& ax, const PassArgs& ay, int gy, long long n)
+template <typename A>
+int enqueue_steps(gp_handle* h, int mode, const A& ax, const A& ay, int gy, long long n)
 {
     for (long long s = 0; s < n; ++s) {
         LK(launch_xpass(ax, mode, h->stream));
@@ -276,9 +374,11 @@ int enqueue_steps(gp_handle* h, int mode, const PassArgs& ax, const PassArgs& ay
 // steps are launched directly.
 constexpr int kGraphSteps = 16;
 
-int run_steps(gp_handle* h, int mode, const PassArgs& ax, const PassArgs& ay, int gy, long long n)
+template <typename A>
+int run_steps(gp_handle* h, int mode, const A& ax, const A& ay, int gy, long long n)
 {
-    if (n >= kGraphSteps && !h->graph[mode]) {
+    cudaGraphExec_t& ge = h->graph[h->active == GP_FP32_MIXED ? 1 : 0][mode];
+    if (n >= kGraphSteps && !ge) {
         // one direct step first: it sets the kernels' shared-memory attributes
         int st = enqueue_steps(h, mode, ax, ay, gy, 1);
         if (st) return st;
@@ -288,16 +388,41 @@ int run_steps(gp_handle* h, int mode, const PassArgs& ax, const PassArgs& ay, in
             int cst = enqueue_steps(h, mode, ax, ay, gy, kGraphSteps);
             cudaError_t e = cudaStreamEndCapture(h->stream, &g);
             if (cst == GP_OK && e == cudaSuccess && g) {
-                if (cudaGraphInstantiate(&h->graph[mode], g, 0) != cudaSuccess) h->graph[mode] = nullptr;
+                if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) ge = nullptr;
             }
             if (g) cudaGraphDestroy(g);
         }
         cudaGetLastError();  // a failed capture only means direct launches
     }
-    if (h->graph[mode]) {
-        for (; n >= kGraphSteps; n -= kGraphSteps) CK(cudaGraphLaunch(h->graph[mode], h->stream));
+    if (ge) {
+        for (; n >= kGraphSteps; n -= kGraphSteps) CK(cudaGraphLaunch(ge, h->stream));
     }
     return enqueue_steps(h, mode, ax, ay, gy, n);
+}
+
+int propagate_active(gp_handle* h, long long nsteps, int mode)
+{
+    int st = ensure_coef(h, mode);
+    if (st) return st;
+    const CoefSet& cs = h->coef[mode];
+    if (mode == GP_REAL && (st = flush_scale(h))) return st;
+    const bool f32 = h->active == GP_FP32_MIXED;
+    const int gy = y_blocks(f32 ? cs.fty : cs.ty);
+    if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
+    if (mode == GP_IMAG) CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    if (f32) {
+        PassArgsF ax = pass_args_f32(h, cs, 0), ay = pass_args_f32(h, cs, 1);
+        if (mode == GP_IMAG) ay.partials = h->partials;
+        st = run_steps(h, mode, ax, ay, gy, nsteps);
+    } else {
+        PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+        if (mode == GP_IMAG) ay.partials = h->partials;
+        st = run_steps(h, mode, ax, ay, gy, nsteps);
+    }
+    if (st) return st;
+    if (mode == GP_IMAG) h->scale_pending = true;
+    h->steps += nsteps;
+    return GP_OK;
 }
 
 }  // namespace
@@ -327,6 +452,7 @@ int gp_create(const gp_params* params, void* cuda_stream, gp_handle** out)
     gp_handle* h = new (std::nothrow) gp_handle();
     if (!h) return GP_ERR_OOM;
     h->p = *params;
+    h->active = params->precision;
     cudaGetDevice(&h->device);
     if (cuda_stream) {
         h->stream = (cudaStream_t)cuda_stream;
@@ -343,15 +469,20 @@ int gp_create(const gp_params* params, void* cuda_stream, gp_handle** out)
               cudaMalloc(&h->partials, kNormBlocksMax * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&h->obs_part, (size_t)obs_blocks(h->p.nx, h->p.ny) * obs_slots() * sizeof(double)) ==
                   cudaSuccess &&
-              cudaMalloc(&h->scal, 2 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&h->scal, 3 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&h->obs_out, 8 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&h->flag, sizeof(int)) == cudaSuccess;
+    if (ok && wants_fp32(h))
+        ok = cudaMalloc(&h->psi32, n * sizeof(float2)) == cudaSuccess &&
+             cudaMalloc(&h->work32, n * sizeof(float2)) == cudaSuccess;
     if (!ok) {
         gp_destroy(h);
         return GP_ERR_OOM;
     }
     if (cudaMemsetAsync(h->psi, 0, n * sizeof(double2), h->stream) != cudaSuccess ||
-        launch_set_scalar(h->scal, 1.0, h->stream) != 0 || cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        (h->psi32 && cudaMemsetAsync(h->psi32, 0, n * sizeof(float2), h->stream) != cudaSuccess) ||
+        launch_set_scalar(h->scal, 1.0, h->stream) != 0 || launch_set_scalar(h->scal + 2, 1.0, h->stream) != 0 ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
         gp_destroy(h);
         return GP_ERR_CUDA;
     }
@@ -364,8 +495,11 @@ void gp_destroy(gp_handle* h)
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto& c : h->coef) free_coef(c);
+    drop_graphs(h);
     cudaFree(h->psi);
     cudaFree(h->work);
+    cudaFree(h->psi32);
+    cudaFree(h->work32);
     cudaFree(h->partials);
     cudaFree(h->obs_part);
     cudaFree(h->scal);
@@ -373,8 +507,6 @@ void gp_destroy(gp_handle* h)
     cudaFree(h->flag);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
-    for (auto& g : h->graph)
-        if (g) cudaGraphExecDestroy(g);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -397,6 +529,7 @@ int gp_set_state(gp_handle* h, const double* psi_host, int normalize)
     if (!h || !psi_host) return GP_ERR_ARG;
     CK(cudaMemcpyAsync(h->psi, psi_host, n_elems(h) * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
     LK(launch_set_scalar(h->scal, 1.0, h->stream));
+    LK(narrow_from_psi(h));
     h->scale_pending = false;
     if (normalize) {
         CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
@@ -413,7 +546,11 @@ int gp_set_state(gp_handle* h, const double* psi_host, int normalize)
 int gp_get_state(gp_handle* h, double* psi_out)
 {
     if (!h || !psi_out) return GP_ERR_ARG;
-    LK(launch_scaled_copy(h->work, h->psi, n_elems(h), h->scal, h->stream));
+    if (h->active == GP_FP32_MIXED) {
+        LK(launch_scaled_copy(h->work, h->psi32, n_elems(h), h->scal, h->stream));
+    } else {
+        LK(launch_scaled_copy(h->work, h->psi, n_elems(h), h->scal, h->stream));
+    }
     CK(cudaMemcpyAsync(psi_out, h->work, n_elems(h) * sizeof(double2), cudaMemcpyDeviceToHost, h->stream));
     return sync_status(h);
 }
@@ -424,6 +561,7 @@ int gp_init_gaussian(gp_handle* h, const double frac[3], unsigned long long seed
     for (int c = 0; c < 3; ++c)
         if (!(frac[c] >= 0) || !is_finite(frac[c])) return GP_ERR_ARG;
     LK(launch_init_gaussian(h->psi, h->p.nx, h->p.ny, h->p.xlen, h->p.ylen, frac, seed, phase_noise, h->stream));
+    LK(narrow_from_psi(h));
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     LK(launch_norm(h->psi, n_elems(h), h->partials, norm_blocks(h), cell(h), h->scal, h->flag, h->stream));
     h->scale_pending = true;
@@ -437,20 +575,22 @@ int gp_propagate(gp_handle* h, long long nsteps, int mode)
 {
     if (!h || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
     if (nsteps == 0) return GP_OK;
-    int st = ensure_coef(h, mode);
+    int st = propagate_active(h, nsteps, mode);
     if (st) return st;
-    const CoefSet& cs = h->coef[mode];
-    if (mode == GP_REAL && (st = flush_scale(h))) return st;
-    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
-    int gy = (cs.ty.nlines + cs.ty.R - 1) / cs.ty.R;
-    if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
-    if (mode == GP_IMAG) {
-        ay.partials = h->partials;
-        CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    return sync_status(h);
+}
+
+int gp_refine_fp64(gp_handle* h, long long nsteps, int mode)
+{
+    if (!h || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
+    if (h->active == GP_FP32_MIXED) {
+        // widen the complex64 state (the pending scale stays pending)
+        LK(widen_into_psi(h));
+        h->active = GP_FP64;
     }
-    if ((st = run_steps(h, mode, ax, ay, gy, nsteps))) return st;
-    if (mode == GP_IMAG) h->scale_pending = true;
-    h->steps += nsteps;
+    if (nsteps == 0) return sync_status(h);
+    int st = propagate_active(h, nsteps, mode);
+    if (st) return st;
     return sync_status(h);
 }
 
@@ -463,13 +603,23 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out)
     if (mode == GP_REAL && (st = flush_scale(h))) return st;
     for (auto& e : h->ev)
         if (!e) CK(cudaEventCreate(&e));
-    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
-    int gy = (cs.ty.nlines + cs.ty.R - 1) / cs.ty.R;
-    if (mode == GP_IMAG) ay.partials = h->partials;
+    const bool f32 = h->active == GP_FP32_MIXED;
+    const int gy = y_blocks(f32 ? cs.fty : cs.ty);
+    if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
     CK(cudaEventRecord(h->ev[0], h->stream));
-    LK(launch_xpass(ax, mode, h->stream));
-    CK(cudaEventRecord(h->ev[1], h->stream));
-    LK(launch_ypass(ay, mode, h->stream));
+    if (f32) {
+        PassArgsF ax = pass_args_f32(h, cs, 0), ay = pass_args_f32(h, cs, 1);
+        if (mode == GP_IMAG) ay.partials = h->partials;
+        LK(launch_xpass(ax, mode, h->stream));
+        CK(cudaEventRecord(h->ev[1], h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
+    } else {
+        PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+        if (mode == GP_IMAG) ay.partials = h->partials;
+        LK(launch_xpass(ax, mode, h->stream));
+        CK(cudaEventRecord(h->ev[1], h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
+    }
     CK(cudaEventRecord(h->ev[2], h->stream));
     if (mode == GP_IMAG) {
         LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
@@ -492,12 +642,21 @@ int gp_apply_substep(gp_handle* h, int which, int mode)
     if (st) return st;
     if ((st = flush_scale(h))) return st;
     const CoefSet& cs = h->coef[mode];
-    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
-    ax.do_p = which == 0;
-    ax.do_solve = which == 1;
-    ay.do_solve = which == 2;
-    LK(launch_xpass(ax, mode, h->stream));
-    LK(launch_ypass(ay, mode, h->stream));
+    if (h->active == GP_FP32_MIXED) {
+        PassArgsF ax = pass_args_f32(h, cs, 0), ay = pass_args_f32(h, cs, 1);
+        ax.do_p = which == 0;
+        ax.do_solve = which == 1;
+        ay.do_solve = which == 2;
+        LK(launch_xpass(ax, mode, h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
+    } else {
+        PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+        ax.do_p = which == 0;
+        ax.do_solve = which == 1;
+        ay.do_solve = which == 2;
+        LK(launch_xpass(ax, mode, h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
+    }
     return sync_status(h);
 }
 
@@ -505,6 +664,7 @@ int gp_observables(gp_handle* h, gp_obs* out)
 {
     if (!h || !out) return GP_ERR_ARG;
     const gp_params& p = h->p;
+    LK(widen_into_psi(h));
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     LK(launch_observables(h->psi, h->scal, p.nx, p.ny, p.xlen, p.ylen, p.wx, p.wy, p.c0, p.c2, p.rabi, p.omeg,
                           gamma_of(p), eta_of(p), h->obs_part, h->obs_out, h->flag, h->stream));

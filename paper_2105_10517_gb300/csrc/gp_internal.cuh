@@ -20,6 +20,10 @@
 // tridiagonal per channel lambda in {+1, 0, -1}:
 //   A = -1/2 D2 + kappa D1,  kappa = i(gamma lambda - Omega y_j)      (x-pass)
 //                            kappa = i(Omega x_i - eta gamma mu)       (y-pass)
+//
+// Both passes exist for complex128 (double2, the FP64 path) and complex64
+// (float2, the FP32-storage path); coefficient tables are always computed in
+// FP64 and stored in the pass's precision; norms are always summed in FP64.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -34,17 +38,20 @@ constexpr int kFix = 64;
 
 // Thomas factorisation of (I + tau A) for one line and one eigen-channel.
 // Row k of the elimination: inv_k = 1/(beta - alpha c'_{k-1}), c'_k = gamma' inv_k,
-// g_k = alpha inv_k.  Entries k >= kHead equal entry kHead-1 to FP64 rounding
-// (the recurrence contracts by |c'|^2 per row), so kernels index min(k, kHead-1).
+// g_k = alpha inv_k.  Entries k >= kHead equal entry kHead-1 to rounding (the
+// recurrence contracts by |c'|^2 per row), so kernels index min(k, kHead-1).
 // pf[t] = (-g_inf)^(t+1) and pb[t] = (-c'_inf)^(t+1) are the influence of a
 // chunk's carry on the t-th element after (forward) or before (backward) it.
-struct LineCoef {
-    double2 inv[kHead];
-    double2 g[kHead];
-    double2 cp[kHead];
-    double2 pf[kFix];
-    double2 pb[kFix];
+template <typename C>
+struct LineCoefT {
+    C inv[kHead];
+    C g[kHead];
+    C cp[kHead];
+    C pf[kFix];
+    C pb[kFix];
 };
+using LineCoef = LineCoefT<double2>;
+using LineCoefF = LineCoefT<float2>;
 
 // Tiling of one line pass (chosen on the host).
 struct LineTiling {
@@ -53,16 +60,17 @@ struct LineTiling {
     int R;      // lines per CTA
     int m;      // chunk length of the parallel Thomas solve
     int Q;      // chunks per line = ceil(L / m)
-    int F;      // fixup length (|c'_inf|^F <= 2^-60), F < m
+    int F;      // fixup length (|c'_inf|^F below the precision's rounding), F < m
     int Lp;     // padded smem stride of one line-channel: Q (m + 1) + 1
     int threads;
     size_t smem;
 };
 
-struct PassArgs {
-    const double2* in;
-    double2* out;
-    const LineCoef* coef;      // [nlines][3]
+template <typename C>
+struct PassArgsT {
+    const C* in;
+    C* out;
+    const LineCoefT<C>* coef;  // [nlines][3]
     LineTiling t;
     int nx, ny;
     int do_p;                  // x-pass: apply the pointwise substep
@@ -70,34 +78,43 @@ struct PassArgs {
     const double* scale;       // device scalar: pending normalisation (x-pass)
     double* partials;          // y-pass: per-CTA sum |psi|^2
     // pointwise substep constants (x-pass)
-    const double2* ex;         // [nx] exp(-tau' wx^2 x^2 / 2)
-    const double2* ey;         // [ny] exp(-tau' wy^2 y^2 / 2)
+    const C* ex;               // [nx] exp(-tau' wx^2 x^2 / 2)
+    const C* ey;               // [ny] exp(-tau' wy^2 y^2 / 2)
     double dt, c0, c2, rabi;
 };
+using PassArgs = PassArgsT<double2>;
+using PassArgsF = PassArgsT<float2>;
 
-}  // namespace gpspin
-
-namespace gpspin {
 int report_cuda(cudaError_t e, const char* what);
 // parameter checks and tiling (gp_capi.cu)
 int validate(const gp_params* p);
 int eta_of(const gp_params& p);
 double gamma_of(const gp_params& p);
 double max_cp(const gp_params& p, int dir, int mode);
-int choose_tiling(int L, int nlines, double cpmax, LineTiling* t);
+// fp32 = 1: tiling for complex64 lines (fixups to 2^-26 instead of 2^-60)
+int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32 = 0);
+
 // launchers (gp_sweeps.cu)
 int launch_coef(LineCoef* coef, int nlines, int dir, int mode, double h, double line_len, double line_h,
                 double dt, double omeg, double gamma, int eta, int* status, cudaStream_t st);
+int launch_coef(LineCoefF* coef, int nlines, int dir, int mode, double h, double line_len, double line_h,
+                double dt, double omeg, double gamma, int eta, int* status, cudaStream_t st);
 int launch_trap_table(double2* out, int n, double len, double w, double dt, int mode, cudaStream_t st);
+int launch_trap_table(float2* out, int n, double len, double w, double dt, int mode, cudaStream_t st);
 int launch_xpass(const PassArgs& a, int mode, cudaStream_t st);
 int launch_ypass(const PassArgs& a, int mode, cudaStream_t st);
+int launch_xpass(const PassArgsF& a, int mode, cudaStream_t st);
+int launch_ypass(const PassArgsF& a, int mode, cudaStream_t st);
 // launchers (gp_reduce.cu)
 int launch_norm(const double2* psi, size_t n, double* partials, int nblk, double da, double* scale, int* flag,
                 cudaStream_t st);
 int launch_finalize_norm(const double* partials, int n, double da, double* scale, int* flag, cudaStream_t st);
 int launch_apply_scale(double2* psi, size_t n, double* scale, cudaStream_t st);
+int launch_apply_scale(float2* psi, size_t n, double* scale, cudaStream_t st);
 int launch_set_scalar(double* p, double v, cudaStream_t st);
 int launch_scaled_copy(double2* dst, const double2* src, size_t n, const double* scale, cudaStream_t st);
+int launch_scaled_copy(double2* dst, const float2* src, size_t n, const double* scale, cudaStream_t st);
+int launch_narrow(float2* dst, const double2* src, size_t n, cudaStream_t st);
 int launch_init_gaussian(double2* psi, int nx, int ny, double xlen, double ylen, const double frac[3],
                          unsigned long long seed, double noise, cudaStream_t st);
 int obs_blocks(int nx, int ny);
@@ -105,4 +122,5 @@ int obs_slots();
 int launch_observables(const double2* psi, const double* scale, int nx, int ny, double xlen, double ylen, double wx,
                        double wy, double c0, double c2, double rabi, double omeg, double gamma, int eta,
                        double* partials, double* out, int* flag, cudaStream_t st);
+
 }  // namespace gpspin

@@ -69,21 +69,35 @@ __global__ void __launch_bounds__(kRedThreads) finalize_norm_kernel(const double
     }
 }
 
-__global__ void apply_scale_kernel(double2* psi, size_t n, double* scale)
+template <typename C>
+__global__ void apply_scale_kernel(C* psi, size_t n, double* scale)
 {
     const double s = scale[0];
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-        double2 v = psi[k];
-        psi[k] = make_double2(s * v.x, s * v.y);
+        C v = psi[k];
+        v.x = s * v.x;
+        v.y = s * v.y;
+        psi[k] = v;
     }
 }
 
-__global__ void scaled_copy_kernel(double2* dst, const double2* src, size_t n, const double* scale)
+// dst = s * src in FP64 (the source is either precision; widening is exact).
+template <typename C>
+__global__ void scaled_copy_kernel(double2* dst, const C* src, size_t n, const double* scale)
 {
     const double s = scale[0];
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        C v = src[k];
+        dst[k] = make_double2(s * (double)v.x, s * (double)v.y);
+    }
+}
+
+// complex128 -> complex64 (round to nearest).
+__global__ void narrow_kernel(float2* dst, const double2* src, size_t n)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
         double2 v = src[k];
-        dst[k] = make_double2(s * v.x, s * v.y);
+        dst[k] = make_float2((float)v.x, (float)v.y);
     }
 }
 
@@ -270,6 +284,13 @@ int launch_apply_scale(double2* psi, size_t n, double* scale, cudaStream_t st)
     return report_cuda(cudaGetLastError(), __func__);
 }
 
+int launch_apply_scale(float2* psi, size_t n, double* scale, cudaStream_t st)
+{
+    apply_scale_kernel<<<grid_for(n, 256, 1216), 256, 0, st>>>(psi, n, scale);
+    set_scalar_kernel<<<1, 1, 0, st>>>(scale, 1.0);
+    return report_cuda(cudaGetLastError(), __func__);
+}
+
 int launch_set_scalar(double* p, double v, cudaStream_t st)
 {
     set_scalar_kernel<<<1, 1, 0, st>>>(p, v);
@@ -279,6 +300,18 @@ int launch_set_scalar(double* p, double v, cudaStream_t st)
 int launch_scaled_copy(double2* dst, const double2* src, size_t n, const double* scale, cudaStream_t st)
 {
     scaled_copy_kernel<<<grid_for(n, 256, 1216), 256, 0, st>>>(dst, src, n, scale);
+    return report_cuda(cudaGetLastError(), __func__);
+}
+
+int launch_scaled_copy(double2* dst, const float2* src, size_t n, const double* scale, cudaStream_t st)
+{
+    scaled_copy_kernel<<<grid_for(n, 256, 1216), 256, 0, st>>>(dst, src, n, scale);
+    return report_cuda(cudaGetLastError(), __func__);
+}
+
+int launch_narrow(float2* dst, const double2* src, size_t n, cudaStream_t st)
+{
+    narrow_kernel<<<grid_for(n, 256, 1216), 256, 0, st>>>(dst, src, n);
     return report_cuda(cudaGetLastError(), __func__);
 }
 

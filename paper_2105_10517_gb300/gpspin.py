@@ -24,7 +24,7 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-
 
 IMAG, REAL = 0, 1
 SO_NONE, SO_RASHBA, SO_DRESSELHAUS = 0, 1, 2
-FP64 = 0
+FP64, FP32_MIXED = 0, 1
 SUB_P, SUB_X, SUB_Y = 0, 1, 2
 
 STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP_ERR_NONFINITE",
@@ -32,7 +32,8 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-           "gp_propagate", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_propagate_noalloc",
+           "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step",
+           "gp_propagate_noalloc",
            "gp_strerror"]
 
 
@@ -123,6 +124,7 @@ def load():
     lib.gp_get_state.argtypes = [vp, dp]
     lib.gp_init_gaussian.argtypes = [vp, dp, ctypes.c_ulonglong, ctypes.c_double]
     lib.gp_propagate.argtypes = [vp, ctypes.c_longlong, ip]
+    lib.gp_refine_fp64.argtypes = [vp, ctypes.c_longlong, ip]
     lib.gp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
     lib.gp_apply_substep.argtypes = [vp, ip, ip]
     lib.gp_profile_step.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_float)]
@@ -131,7 +133,7 @@ def load():
     lib.gp_strerror.argtypes = [ip]
     lib.gp_strerror.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-                 "gp_propagate", "gp_observables", "gp_apply_substep", "gp_profile_step"):
+                 "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -243,6 +245,10 @@ class Solver:
 
     def propagate(self, nsteps, mode=IMAG):
         _check(load().gp_propagate(self._h, int(nsteps), int(mode)), "gp_propagate")
+
+    def refine_fp64(self, nsteps, mode=IMAG):
+        """Widen an FP32-storage handle to FP64 and continue nsteps steps in FP64."""
+        _check(load().gp_refine_fp64(self._h, int(nsteps), int(mode)), "gp_refine_fp64")
 
     def apply_substep(self, which, mode=IMAG):
         w = {"P": SUB_P, "X": SUB_X, "Y": SUB_Y}.get(which, which)
