@@ -48,7 +48,7 @@ INST_PER_SITE = {"xpass": 165, "ypass": 63}
 BYTES_PER_SITE_PASS = 96
 # DRAM traffic of one launch from an ncu capture (profiles/), keyed by kernel
 # and valid only while the kernel source is unchanged (sha256 prefix).
-NCU_TRAFFIC = {"xpass_kernel<0> vortex512": (16195584 + 0, "9b9e02dd3793dbcc")}  # profiles/xpass_vortex512.md
+NCU_TRAFFIC = {}
 
 L2_FLUSH_BYTES = 256 << 20
 
@@ -70,21 +70,28 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, help="vortex512 (default), quench1024 or precision2048")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
+                    help="storage precision (default: fp64; precision2048 defaults to fp32)")
     return ap.parse_args()
 
 
-def workload():
+def workload(name=WORKLOAD):
     from paper_2105_10517_gb300 import inputs
-    c = dict(inputs.CONFIGS[WORKLOAD])
+    c = dict(inputs.CONFIGS[name])
     return c, inputs.physics(c)
 
 
-def config_dict(c):
+def config_dict(c, name=WORKLOAD, precision="fp64"):
+    so = {0: "no SO", 1: "Rashba", 2: "Dresselhaus"}[c["so_type"]]
+    mode = "imaginary" if c["mode"] == 0 else "real"
+    half = c["xlen"] / 2
     return {
-        "workload": f"{WORKLOAD}: {c['nx']}x{c['ny']} imaginary-time vortex lattice, [-16,16]^2, dt={c['dt']}, "
-                    f"c0={c['c0']}, c2={c['c2']}, Omega={c['omeg']}, Rashba gamma={c['gamma']}, R={c['rabi']}",
-        "nx": c["nx"], "ny": c["ny"], "dt": c["dt"], "mode": "imaginary",
-        "step": "one split-step CN time step: normalise, P, X sweep, Y sweep, norm",
+        "workload": f"{name}: {c['nx']}x{c['ny']} {mode}-time, [-{half:g},{half:g}]^2, dt={c['dt']}, "
+                    f"c0={c['c0']}, c2={c['c2']}, Omega={c['omeg']}, {so} gamma={c['gamma']}, R={c['rabi']}",
+        "nx": c["nx"], "ny": c["ny"], "dt": c["dt"], "mode": mode, "storage": precision,
+        "step": "one split-step CN time step: normalise, P, X sweep, Y sweep" + (", norm" if mode == "imaginary"
+                                                                                  else ""),
         "l2": "flushed by a 256 MiB device write before every timed step",
         "parallelism": "replicas",
     }
@@ -177,14 +184,18 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     gpspin.build()
-    c, p = workload()
+    name = args.workload
+    prec = args.precision or ("fp32" if name == "precision2048" else "fp64")
+    c, p = workload(name)
+    p["precision"] = gpspin.FP32_MIXED if prec == "fp32" else gpspin.FP64
+    mode = c["mode"]
     sites = c["nx"] * c["ny"]
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     s = gpspin.Solver(p, stream=stream.cuda_stream)
     s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
     for _ in range(max(3, args.warmup)):
-        s.profile_step(gpspin.IMAG)
+        s.profile_step(mode)
 
     def barrier():
         torch.cuda.synchronize()
@@ -200,13 +211,13 @@ def run_ours(args):
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
-        per.append(s.profile_step(gpspin.IMAG))
+        per.append(s.profile_step(mode))
     barrier()
     wall = time.perf_counter() - t0
     # keep the GPU busy until the sampler has seen the load a few times
     t1 = time.perf_counter()
     while len(clocks.lines) < 5 and time.perf_counter() - t1 < 3.0:
-        s.propagate(20, gpspin.IMAG)
+        s.propagate(20, mode)
     clocks.stop()
 
     ms_x = statistics.fmean(q[0] for q in per)
@@ -225,14 +236,14 @@ def run_ours(args):
         hout = torch.empty_like(hin).pin_memory()
         for _ in range(3):
             s.set_state(hin)
-            s.propagate(1, gpspin.IMAG)
+            s.propagate(1, mode)
             s.get_state(hout)
         barrier()
         te = time.perf_counter()
         a, b = hin, hout
         for _ in range(args.e2e_steps):
             s.set_state(a)
-            s.propagate(1, gpspin.IMAG)
+            s.propagate(1, mode)
             s.get_state(b)
             a, b = b, a
         barrier()
@@ -244,34 +255,46 @@ def run_ours(args):
 
     dom = "xpass" if ms_x >= ms_y else "ypass"
     ms_dom = ms_x if dom == "xpass" else ms_y
-    achieved = FLOPS_PER_SITE[dom] * sites / (ms_dom / 1e3) / 1e12
-    key = f"{dom}_kernel<0> {WORKLOAD}"
-    tr = NCU_TRAFFIC.get(key)
-    traffic = tr[0] if tr and tr[1] == sha_kernels() else None
-    roofline = {
-        "bound": "alu", "kernel": f"{dom}_kernel<0> (FP64)", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-        "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-        "peak_source": "derived: 2 FP64 FMA lanes/SM/clk x 152 SMs x 2.07 GHz x 2 flop",
-        "fp64_issue_frac": INST_PER_SITE[dom] * sites / (ms_dom / 1e3) / (FP64_PEAK_TFLOPS / 2 * 1e12),
-        "flops_per_launch": FLOPS_PER_SITE[dom] * sites, "traffic": traffic,
-        "hbm_frac_of_measured": None,
-        "kernel_ms": {"xpass": ms_x, "ypass": ms_y, "normalise": ms_n},
-    }
+    kname = f"{dom}_kernel<{mode}, {'float2' if prec == 'fp32' else 'double2'}>"
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         hbm = float(peaks["hbm_gbs"])
-        roofline["hbm_frac_of_measured"] = BYTES_PER_SITE_PASS * 2 * sites / (ms_step / 1e3) / 1e9 / hbm
-        roofline["hbm_peak_gbs"] = hbm
     except (OSError, KeyError, ValueError):
-        pass
+        hbm, peaks = 6800.0, None
+    tr = NCU_TRAFFIC.get(f"{kname} {name}")
+    traffic = tr[0] if tr and tr[1] == sha_kernels() else None
+    if prec == "fp64":
+        achieved = FLOPS_PER_SITE[dom] * sites / (ms_dom / 1e3) / 1e12
+        roofline = {
+            "bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": "derived: 2 FP64 FMA lanes/SM/clk x 152 SMs x 2.07 GHz x 2 flop",
+            "fp64_issue_frac": INST_PER_SITE[dom] * sites / (ms_dom / 1e3) / (FP64_PEAK_TFLOPS / 2 * 1e12),
+            "flops_per_launch": FLOPS_PER_SITE[dom] * sites,
+        }
+        bytes_site_pass = BYTES_PER_SITE_PASS
+    else:
+        bytes_site_pass = BYTES_PER_SITE_PASS // 2
+        achieved = bytes_site_pass * sites / (ms_dom / 1e3) / 1e9
+        roofline = {
+            "bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm,
+            "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback",
+            "bytes_per_launch": bytes_site_pass * sites,
+        }
+    roofline["traffic"] = traffic
+    roofline["kernel_ms"] = {"xpass": ms_x, "ypass": ms_y, "normalise": ms_n}
+    roofline["step_hbm_frac_of_measured"] = bytes_site_pass * 2 * sites / (ms_step / 1e3) / 1e9 / hbm
+    roofline["hbm_peak_gbs"] = hbm
 
     out = None
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian + splitmix64 phase noise)",
-            "config": config_dict(c), "roofline": roofline, "e2e": e2e,
+            "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic (seeded Gaussian + splitmix64 phase noise)",
+            "config": config_dict(c, name, prec), "roofline": roofline, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "clocks": clocks.summary(), "wall_s_timed_loop": wall,
         }
     s.close()
@@ -282,7 +305,7 @@ def run_ours(args):
 
 
 # ----------------------------------------------------------- CPU oracle ----
-def oracle_rate(p, nx, steps, seconds=None):
+def oracle_rate(p, nx, steps, seconds=None, mode=0):
     """Oracle site-steps/s on an nx x nx grid with the workload's dx, dt and physics."""
     import oracle
     from paper_2105_10517_gb300 import inputs
@@ -291,7 +314,7 @@ def oracle_rate(p, nx, steps, seconds=None):
     psi = inputs.gaussian_state(nx, nx, q["xlen"], q["ylen"], seed=2)
     done, t0 = 0, time.perf_counter()
     while True:
-        psi = oracle.step(q, psi, oracle.IMAG)
+        psi = oracle.step(q, psi, mode)
         done += 1
         el = time.perf_counter() - t0
         if (steps is not None and done >= steps) or (seconds is not None and el >= seconds and done >= 2):
@@ -299,10 +322,11 @@ def oracle_rate(p, nx, steps, seconds=None):
     return nx * nx * done / el, done, el
 
 
-def cpu_baseline(p, seconds):
-    rate, done, el = oracle_rate(p, p["nx"], None, seconds)
+def cpu_baseline(p, seconds, mode=0):
+    rate, done, el = oracle_rate(p, p["nx"], None, seconds, mode)
+    kind = "imaginary" if mode == 0 else "real"
     return {"value": rate / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} imaginary-time steps of the full {p['nx']}x{p['ny']} workload "
+            "sample": f"{done} {kind}-time steps of the full {p['nx']}x{p['ny']} workload "
                       f"({el:.1f} s, single-threaded C oracle)"}
 
 
@@ -311,20 +335,21 @@ def run_reference(args):
         return None
     import oracle
     oracle.build()
-    c, p = workload()
+    c, p = workload(args.workload)
     # calibrate: size the sample grid so that warmup + steps take about two minutes
-    r, _, _ = oracle_rate(p, 64, 3)
+    r, _, _ = oracle_rate(p, 64, 3, mode=c["mode"])
     budget = 120.0 / max(1, args.steps + args.warmup)
     n = int(max(16, min(p["nx"], math.sqrt(budget * r))))
-    oracle_rate(p, n, max(1, args.warmup))
-    rate, done, el = oracle_rate(p, n, args.steps)
+    oracle_rate(p, n, max(1, args.warmup), mode=c["mode"])
+    rate, done, el = oracle_rate(p, n, args.steps, mode=c["mode"])
     value = rate / 1e6
     sample = (f"{n}x{n} grid with the {p['nx']}x{p['ny']} workload's dx, dt and physics, "
               f"{done} timed steps after {args.warmup} warm-up steps ({el:.1f} s)")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian)", "config": config_dict(c),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian)",
+        "config": config_dict(c, args.workload),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -342,8 +367,8 @@ def main():
     if out is not None:
         world = out["n_gpus"]
         if world == 1 and not args.no_cpu_baseline:
-            _, p = workload()
-            out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds)
+            c, p = workload(args.workload)
+            out["cpu_baseline"] = cpu_baseline(p, args.cpu_seconds, c["mode"])
         print(json.dumps(out))
 
 

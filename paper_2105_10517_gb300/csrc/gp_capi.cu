@@ -138,7 +138,8 @@ int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32)
         Q = (L + m - 1) / m;
     }
     int Lp = Q * (m + 1) + 1;
-    auto smem_of = [&](int R) { return (size_t)(2 * 3 * R * Lp + 2 * 3 * R * Q) * elem; };
+    auto up = [](size_t b) { return (b + 127) / 128 * 128; };
+    auto smem_of = [&](int R) { return up(3 * R * Lp * elem) * 2 + 2 * up(3 * R * Q * elem); };
     int R = std::max(1, 256 / (3 * Q));
     if (fp32) R = std::max(R, 4);  // >= 32-byte segments in the transposed store
     while (R > 1 && (smem_of(R) > 100 * 1024 || 3 * R * Q > 512)) --R;
@@ -154,6 +155,10 @@ int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32)
     int thr = std::max(64, 3 * R * Q);
     t->threads = std::min(512, (thr + 31) / 32 * 32);
     t->smem = smem_of(R);
+    t->off_b = up(3 * R * Lp * elem);
+    t->off_cf = 2 * t->off_b;
+    t->off_cb = t->off_cf + up(3 * R * Q * elem);
+    t->bulk = 0;  // set per pass by the caller (needs 16-byte aligned rows)
     return GP_OK;
 }
 
@@ -265,6 +270,16 @@ void fill_common(gp_handle* h, PassArgsT<C>& a)
     a.rabi = h->p.rabi;
     a.do_p = 1;
     a.do_solve = 1;
+    a.err = h->flag;
+}
+
+// Rows can be staged with cp.async.bulk when every row starts on a 16-byte
+// boundary and its size is a multiple of 16 bytes.
+template <typename C>
+void set_bulk(PassArgsT<C>& a, int dir, int nx, int ny)
+{
+    const int L = dir == 0 ? nx : ny;
+    a.t.bulk = ((size_t)L * sizeof(C)) % 16 == 0 ? 1 : 0;
 }
 
 PassArgs pass_args(gp_handle* h, const CoefSet& cs, int dir)
@@ -284,6 +299,7 @@ PassArgs pass_args(gp_handle* h, const CoefSet& cs, int dir)
         a.coef = cs.cy;
         a.t = cs.ty;
     }
+    set_bulk(a, dir, h->p.nx, h->p.ny);
     return a;
 }
 
@@ -304,6 +320,7 @@ PassArgsF pass_args_f32(gp_handle* h, const CoefSet& cs, int dir)
         a.coef = cs.fy;
         a.t = cs.fty;
     }
+    set_bulk(a, dir, h->p.nx, h->p.ny);
     return a;
 }
 

@@ -64,6 +64,10 @@ struct LineTiling {
     int Lp;     // padded smem stride of one line-channel: Q (m + 1) + 1
     int threads;
     size_t smem;
+    size_t off_b;  // byte offsets in dynamic smem of the second line array (also the
+    size_t off_cf; // staging area of the bulk row copies) and of the carry arrays
+    size_t off_cb;
+    int bulk;      // rows are 16-byte aligned: stage them with cp.async.bulk
 };
 
 template <typename C>
@@ -77,6 +81,7 @@ struct PassArgsT {
     int do_solve;              // apply the CN solve (0: channels pass through)
     const double* scale;       // device scalar: pending normalisation (x-pass)
     double* partials;          // y-pass: per-CTA sum |psi|^2
+    int* err;                  // status bits set by the kernel (8: bulk-copy wait timed out)
     // pointwise substep constants (x-pass)
     const C* ex;               // [nx] exp(-tau' wx^2 x^2 / 2)
     const C* ey;               // [ny] exp(-tau' wy^2 y^2 / 2)

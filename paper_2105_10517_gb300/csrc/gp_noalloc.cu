@@ -141,6 +141,9 @@ extern "C" int gp_propagate_noalloc(const gp_params* params, double* psi_dev, lo
     ay.out = reinterpret_cast<double2*>(psi_dev);
     ay.coef = S.cy;
     ay.t = ty;
+    ax.err = ay.err = S.flag;
+    ax.t.bulk = ((size_t)p.nx * sizeof(double2)) % 16 == 0 && (reinterpret_cast<uintptr_t>(psi_dev) % 16) == 0;
+    ay.t.bulk = ((size_t)p.ny * sizeof(double2)) % 16 == 0;
     const double da = dx * dy;
     const int gy = (ty.nlines + ty.R - 1) / ty.R;
     if (mode == GP_IMAG) ay.partials = S.partials;

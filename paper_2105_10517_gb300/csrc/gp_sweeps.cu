@@ -51,6 +51,79 @@ template <> __device__ __forceinline__ float2 store_as<float2>(double2 v)
     return make_float2((float)v.x, (float)v.y);
 }
 
+// ------------------------------------------------- bulk row copies (TMA) ---
+// Whole input rows are staged into shared memory with cp.async.bulk (the
+// Blackwell bulk-copy engine), completing on an mbarrier, so every row of the
+// CTA is in flight at once instead of one global load per loop iteration.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(m)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* m)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on phase 0 of the barrier.  Returns true (for the whole CTA) once
+// the copies have landed; if any thread gives up after kWaitTries polls, the
+// CTA sets bit 8 of *err, waits once more (again bounded) so that no copy is
+// still writing its shared memory, and returns false.
+constexpr int kWaitTries = 1 << 22;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err)
+{
+    bool ok = false;
+    for (int it = 0; it < kWaitTries && !ok; ++it) ok = mbar_try_wait(m, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0 && err) atomicOr(err, 8);
+        for (int it = 0; it < kWaitTries && !ok; ++it) ok = mbar_try_wait(m, 0);
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// Stages rows row(r, c) = base + (c * plane + (line0 + r) * L) of length L for
+// r < nl, c < 3 into dst[(r * 3 + c) * L].  Rows must be 16-byte aligned.
+template <typename C>
+__device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, int line0, int nl, int L,
+                                           uint64_t* mbar, int* err)
+{
+    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t row_bytes = (uint32_t)(L * sizeof(C));
+        mbar_expect_tx(mbar, row_bytes * 3u * (uint32_t)nl);
+        for (int r = 0; r < nl; ++r)
+            for (int c = 0; c < 3; ++c)
+                bulk_g2s(dst + (size_t)(r * 3 + c) * L, base + c * plane + (size_t)(line0 + r) * L, row_bytes, mbar);
+    }
+    return mbar_wait_bounded(mbar, err);
+}
+
 // ------------------------------------------------------------------ K1 ----
 // One thread per (line, channel), always in FP64 (stored in the pass's
 // precision).  The line operator is A = -1/2 D2 + kappa D1 with kappa = i kb;
@@ -347,14 +420,24 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
     const int start = q * m;
     const int len = min(m, L - start);
     const LineCoefT<C>* Co = coef + lc;   // coef already offset to the CTA's first line
-    C* pa = sa + lc * Lp + q * (m + 1);
-    C* pbf = sb + lc * Lp + q * (m + 1);
+    C* __restrict__ pa = sa + lc * Lp + q * (m + 1);
+    C* __restrict__ pbf = sb + lc * Lp + q * (m + 1);
 
+    // Converged factorisation (rows >= kHead - 1) in registers; rows inside the
+    // table head are fetched with a predicated load (no divergent branch).
+    const C inv_c = Co->inv[kHead - 1], g_c = Co->g[kHead - 1], cp_c = Co->cp[kHead - 1];
     if (active) {
         C y = mkc<C>(R(0), R(0));
+#pragma unroll 4
         for (int t = 0; t < len; ++t) {
-            int kk = min(start + t, kHead - 1);
-            y = cfnma(Co->g[kk], y, cmul(Co->inv[kk], pa[t]));
+            const int k = start + t;
+            const bool head = k < kHead - 1;
+            C inv = inv_c, g = g_c;
+            if (head) {
+                inv = Co->inv[k];
+                g = Co->g[k];
+            }
+            y = cfnma(g, y, cmul(inv, pa[t]));
             pbf[t] = y;
         }
         cf[lc * Q + q] = y;
@@ -367,9 +450,12 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
             for (int t = 0; t < nf; ++t) pbf[t] = cfma(Co->pf[t], yc, pbf[t]);
         }
         C w = mkc<C>(R(0), R(0));
+#pragma unroll 4
         for (int t = len - 1; t >= 0; --t) {
-            int kk = min(start + t, kHead - 1);
-            w = cfnma(Co->cp[kk], w, pbf[t]);
+            const int k = start + t;
+            C cp = cp_c;
+            if (k < kHead - 1) cp = Co->cp[k];
+            w = cfnma(cp, w, pbf[t]);
             pbf[t] = w;
         }
         cb[lc * Q + q] = w;
@@ -378,10 +464,11 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
     if (active) {
         const bool fix = q < Q - 1;
         C wc = fix ? cb[lc * Q + q + 1] : mkc<C>(R(0), R(0));
+        const int tf = fix ? len - F : len;  // points t >= tf get the backward fixup
+#pragma unroll 4
         for (int t = 0; t < len; ++t) {
             C w = pbf[t];
-            int d = len - t;
-            if (fix && d <= F) w = cfma(Co->pb[d - 1], wc, w);
+            if (t >= tf) w = cfma(Co->pb[len - t - 1], wc, w);
             C ph = pa[t];
             pa[t] = mkc<C>(fma(R(2), w.x, -ph.x), fma(R(2), w.y, -ph.y));
         }
@@ -393,20 +480,22 @@ __device__ __forceinline__ int sidx(const LineTiling& T, int lc, int k) { return
 
 // --------------------------------------------------------------- x-pass ----
 template <int MODE, typename C>
-__global__ void __launch_bounds__(1024) xpass_kernel(PassArgsT<C> A)
+__global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
 {
     typedef typename RealOf<C>::type R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* smem = reinterpret_cast<C*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
     const LineTiling& T = A.t;
-    C* sa = smem;
-    C* sb = sa + 3 * T.R * T.Lp;
-    C* cf = sb + 3 * T.R * T.Lp;
-    C* cb = cf + 3 * T.R * T.Q;
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = reinterpret_cast<C*>(smem_raw + T.off_b);
+    C* cf = reinterpret_cast<C*>(smem_raw + T.off_cf);
+    C* cb = reinterpret_cast<C*>(smem_raw + T.off_cb);
     const int line0 = blockIdx.x * T.R;
     const int nl = min(T.R, T.nlines - line0);
     const int nx = A.nx, ny = A.ny, L = T.L;
     const size_t plane = (size_t)nx * ny;
+    // stage the CTA's rows psi[c][j][*] into sb (contiguous [r][c][i])
+    if (T.bulk && !stage_rows(sb, A.in, plane, line0, nl, L, &mbar, A.err)) return;
 
     const double s = *A.scale;
     PConstT<R> k;
@@ -416,8 +505,18 @@ __global__ void __launch_bounds__(1024) xpass_kernel(PassArgsT<C> A)
     k.s = R(s);
     for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
         int r = e / L, i = e - r * L, j = line0 + r;
-        size_t o = (size_t)j * nx + i;
-        C a = A.in[o], b = A.in[plane + o], c = A.in[2 * plane + o];
+        C a, b, c;
+        if (T.bulk) {
+            const C* row = sb + (size_t)r * 3 * L + i;
+            a = row[0];
+            b = row[L];
+            c = row[2 * L];
+        } else {
+            size_t o = (size_t)j * nx + i;
+            a = A.in[o];
+            b = A.in[plane + o];
+            c = A.in[2 * plane + o];
+        }
         if (A.do_p) {
             // the trap factor is real in imaginary time
             C ev = MODE == 1 ? cmul(A.ex[i], A.ey[j]) : mkc<C>(A.ex[i].x * A.ey[j].x, R(0));
@@ -451,28 +550,37 @@ __global__ void __launch_bounds__(1024) xpass_kernel(PassArgsT<C> A)
 // Partial norms: each thread sums its sites' |psi|^2 in the pass's precision
 // (a few dozen sites), the CTA then adds the threads' sums in FP64.
 template <int MODE, typename C>
-__global__ void __launch_bounds__(1024) ypass_kernel(PassArgsT<C> A)
+__global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
 {
     typedef typename RealOf<C>::type R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* smem = reinterpret_cast<C*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
     __shared__ double wsum[32];
     const LineTiling& T = A.t;
-    C* sa = smem;
-    C* sb = sa + 3 * T.R * T.Lp;
-    C* cf = sb + 3 * T.R * T.Lp;
-    C* cb = cf + 3 * T.R * T.Q;
+    C* sa = reinterpret_cast<C*>(smem_raw);
+    C* sb = reinterpret_cast<C*>(smem_raw + T.off_b);
+    C* cf = reinterpret_cast<C*>(smem_raw + T.off_cf);
+    C* cb = reinterpret_cast<C*>(smem_raw + T.off_cb);
     const int line0 = blockIdx.x * T.R;
     const int nl = min(T.R, T.nlines - line0);
     const int nx = A.nx, ny = A.ny, L = T.L;
     const size_t plane = (size_t)nx * ny;
+    // stage the CTA's rows t[mu][i][*] into sb (contiguous [r][mu][j])
+    if (T.bulk && !stage_rows(sb, A.in, plane, line0, nl, L, &mbar, A.err)) return;
 
     for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
         int r = e / L, j = e - r * L, i = line0 + r;
-        size_t o = (size_t)i * ny + j;
-        sa[sidx(T, r * 3 + 0, j)] = A.in[o];
-        sa[sidx(T, r * 3 + 1, j)] = A.in[plane + o];
-        sa[sidx(T, r * 3 + 2, j)] = A.in[2 * plane + o];
+        if (T.bulk) {
+            const C* row = sb + (size_t)r * 3 * L + j;
+            sa[sidx(T, r * 3 + 0, j)] = row[0];
+            sa[sidx(T, r * 3 + 1, j)] = row[L];
+            sa[sidx(T, r * 3 + 2, j)] = row[2 * L];
+        } else {
+            size_t o = (size_t)i * ny + j;
+            sa[sidx(T, r * 3 + 0, j)] = A.in[o];
+            sa[sidx(T, r * 3 + 1, j)] = A.in[plane + o];
+            sa[sidx(T, r * 3 + 2, j)] = A.in[2 * plane + o];
+        }
     }
     __syncthreads();
     if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, nl);
