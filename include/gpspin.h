@@ -33,7 +33,8 @@ typedef enum {
     GP_ERR_CUDA = 3,      /* a CUDA runtime call failed; the handle should be destroyed   */
     GP_ERR_NONFINITE = 4, /* a reduction met NaN/Inf in psi; the state is kept as is      */
     GP_ERR_UNSUPPORTED = 5,/* parameters outside what the tabulated solver supports       */
-    GP_ERR_TOO_LARGE = 6  /* grid larger than the fixed scratch of gp_propagate_noalloc    */
+    GP_ERR_TOO_LARGE = 6, /* grid larger than the fixed scratch of gp_propagate_noalloc    */
+    GP_ERR_TIMEOUT = 7    /* a bounded device-side wait gave up; the state is unreliable   */
 } gp_status;
 
 typedef enum { GP_IMAG = 0, GP_REAL = 1 } gp_mode;
@@ -158,6 +159,43 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out);
  * threads) race and corrupt each other's results.  Synchronous with respect to
  * cuda_stream. */
 int gp_propagate_noalloc(const gp_params* params, double* psi_dev, long long nsteps, int mode, void* cuda_stream);
+
+/* ---- Served, batched solves --------------------------------------------------
+ * Many imaginary-time solves of different grids and parameters advance together
+ * (the batched and served forms of the hot path; the paper runs one solve per
+ * program invocation).  A batch admits requests in arrival order while their
+ * device-memory footprint fits in max_device_bytes, keeps each admitted solve's
+ * psi and coefficient tables resident, advances all running solves of one
+ * storage precision with one launch per substep (check_every steps per
+ * gp_batch_step), checks convergence between ticks and retires finished solves,
+ * freeing their memory for the next admission.  A solve's result is the same
+ * alone and in any mix (bitwise: each CTA runs the single-instance arithmetic). */
+typedef struct gp_batch gp_batch;
+typedef enum { GP_REQ_QUEUED = 0, GP_REQ_RUNNING = 1, GP_REQ_DONE = 2, GP_REQ_FAILED = 3, GP_REQ_UNKNOWN = 4 } gp_req_state;
+typedef enum { GP_POLICY_FP64 = 0, GP_POLICY_FP32_REFINE = 1 } gp_policy;
+
+typedef struct {
+    double frac[3];           /* initial state as gp_init_gaussian                          */
+    unsigned long long seed;
+    double phase_noise;
+    double tol;               /* done when |E_k - E_(k-1)| < tol between checks (FP64 phase) */
+    double tol32;             /* GP_POLICY_FP32_REFINE: leave FP32 when |dE| <= tol32 |E|     */
+    long long cap;            /* step cap (a capped solve is reported as done)               */
+    int policy;               /* gp_policy: FP64 throughout, or FP32 then FP64 refinement    */
+} gp_request;
+
+/* Device bytes one solve with these parameters and policy occupies. */
+size_t gp_request_bytes(const gp_params* params, int policy);
+int gp_batch_create(size_t max_device_bytes, int check_every, void* cuda_stream, gp_batch** out);
+void gp_batch_destroy(gp_batch* b);
+/* Queues a solve (params.precision is set from the policy); *id_out identifies it. */
+int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req, long long* id_out);
+/* One tick: admit, advance every running solve by check_every steps, check, retire, admit. */
+int gp_batch_step(gp_batch* b, int* n_running, int* n_queued);
+/* State (gp_req_state), steps taken and last observables of a solve; psi_out
+ * (complex128, may be NULL) receives the result once it is done; release != 0
+ * forgets a finished solve. */
+int gp_batch_poll(gp_batch* b, long long id, int* state, long long* steps, gp_obs* obs, double* psi_out, int release);
 
 /* Human-readable text for a gp_status. */
 const char* gp_strerror(int status);

@@ -1,0 +1,355 @@
+// gp_batch.cu -- many GP solves served together: admission by device-memory
+// footprint, one launch per substep for all running instances of a precision,
+// convergence checks between ticks, retirement that frees memory for the next
+// admission (continuous batching).  Each instance keeps its psi, intermediate
+// and Thomas coefficient tables resident on the device for its whole life.
+//
+// An instance's arithmetic is the same alone and in any mix: batched CTAs run
+// the single-instance kernel bodies with the instance's own tiling and thread
+// count, and its normalisation sums the same partials in the same order.
+#include "gp_handle.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <deque>
+#include <map>
+#include <new>
+#include <vector>
+
+using namespace gpspin;
+
+namespace {
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t cap = 0;
+    int reserve(size_t n)
+    {
+        if (n <= cap) return GP_OK;
+        cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t c = std::max<size_t>(n, 64);
+        if (cudaMalloc(&p, c * sizeof(T)) != cudaSuccess) return GP_ERR_OOM;
+        cap = c;
+        return GP_OK;
+    }
+    void release()
+    {
+        cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct Request {
+    long long id = 0;
+    gp_params p{};
+    gp_request r{};
+    int state = GP_REQ_QUEUED;
+    gp_handle* h = nullptr;
+    size_t bytes = 0;
+    long long steps = 0;
+    bool have_e = false;
+    double e_last = 0;
+    gp_obs obs{};
+    std::vector<double> psi;  // result, complex128, after completion
+};
+
+template <typename C>
+struct Group {
+    std::vector<PassArgsT<C>> ax, ay;
+    std::vector<int2> ix, iy;
+    std::vector<FinArgs> fin;
+    int tx = 0, ty = 0;
+    size_t sx = 0, sy = 0;
+    DevBuf<PassArgsT<C>> dax, day;
+    DevBuf<int2> dix, diy;
+    DevBuf<FinArgs> dfin;
+    void clear()
+    {
+        ax.clear();
+        ay.clear();
+        ix.clear();
+        iy.clear();
+        fin.clear();
+        tx = ty = 0;
+        sx = sy = 0;
+    }
+    void release()
+    {
+        dax.release();
+        day.release();
+        dix.release();
+        diy.release();
+        dfin.release();
+    }
+};
+
+}  // namespace
+
+struct gp_batch {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t max_bytes = 0, used_bytes = 0;
+    int check_every = 100;
+    long long next_id = 1;
+    std::deque<long long> queue;
+    std::map<long long, Request> reqs;
+    Group<double2> g64;
+    Group<float2> g32;
+    int* counts = nullptr;  // device: [n_x64, n_y64, n_inst64, n_x32, n_y32, n_inst32]
+    int* flag = nullptr;
+};
+
+namespace {
+
+#define BK(x)                                                  \
+    do {                                                       \
+        if (report_cuda((x), #x) != 0) return GP_ERR_CUDA;     \
+    } while (0)
+
+int policy_precision(int policy) { return policy == GP_POLICY_FP32_REFINE ? GP_FP32_MIXED : GP_FP64; }
+
+// Puts one running instance into its precision group's launch lists.
+template <typename C>
+void add_instance(Group<C>& g, gp_handle* h, const PassArgsT<C>& ax, PassArgsT<C> ay)
+{
+    const int inst = (int)g.ax.size();
+    ay.partials = h->partials;
+    g.ax.push_back(ax);
+    g.ay.push_back(ay);
+    const int cx = y_blocks(ax.t), cy = y_blocks(ay.t);
+    for (int c = 0; c < cx; ++c) g.ix.push_back(make_int2(inst, c));
+    for (int c = 0; c < cy; ++c) g.iy.push_back(make_int2(inst, c));
+    g.fin.push_back(FinArgs{h->partials, cy, cell(h), h->scal});
+    g.tx = std::max(g.tx, ax.t.threads);
+    g.ty = std::max(g.ty, ay.t.threads);
+    g.sx = std::max(g.sx, ax.t.smem);
+    g.sy = std::max(g.sy, ay.t.smem);
+}
+
+template <typename C>
+int upload_and_run(gp_batch* b, Group<C>& g, int* counts, int steps)
+{
+    if (g.ax.empty()) return GP_OK;
+    int st;
+    if ((st = g.dax.reserve(g.ax.size())) || (st = g.day.reserve(g.ay.size())) || (st = g.dix.reserve(g.ix.size())) ||
+        (st = g.diy.reserve(g.iy.size())) || (st = g.dfin.reserve(g.fin.size())))
+        return st;
+    cudaStream_t s = b->stream;
+    BK(cudaMemcpyAsync(g.dax.p, g.ax.data(), g.ax.size() * sizeof(g.ax[0]), cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(g.day.p, g.ay.data(), g.ay.size() * sizeof(g.ay[0]), cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(g.dix.p, g.ix.data(), g.ix.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(g.diy.p, g.iy.data(), g.iy.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(g.dfin.p, g.fin.data(), g.fin.size() * sizeof(FinArgs), cudaMemcpyHostToDevice, s));
+    const int n[3] = {(int)g.ix.size(), (int)g.iy.size(), (int)g.fin.size()};
+    BK(cudaMemcpyAsync(counts, n, sizeof(n), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < steps; ++k) {
+        if (launch_xpass_batched(g.dax.p, g.dix.p, counts, n[0], g.tx, g.sx, GP_IMAG, s)) return GP_ERR_CUDA;
+        if (launch_ypass_batched(g.day.p, g.diy.p, counts + 1, n[1], g.ty, g.sy, GP_IMAG, s)) return GP_ERR_CUDA;
+        if (launch_finalize_norm_batched(g.dfin.p, counts + 2, n[2], b->flag, s)) return GP_ERR_CUDA;
+    }
+    return GP_OK;
+}
+
+void retire(gp_batch* b, Request& q, int state)
+{
+    if (q.h) {
+        q.psi.resize(2 * n_elems(q.h));
+        if (gp_get_state(q.h, q.psi.data()) != GP_OK) {
+            q.psi.clear();
+            state = GP_REQ_FAILED;
+        }
+        gp_destroy(q.h);
+        q.h = nullptr;
+        b->used_bytes -= q.bytes;
+    }
+    q.state = state;
+}
+
+// Admits queued requests in arrival order while their footprint fits.
+int admit(gp_batch* b)
+{
+    while (!b->queue.empty()) {
+        Request& q = b->reqs[b->queue.front()];
+        if (q.bytes > b->max_bytes) {  // can never fit
+            q.state = GP_REQ_FAILED;
+            b->queue.pop_front();
+            continue;
+        }
+        if (b->used_bytes + q.bytes > b->max_bytes) break;
+        gp_handle* h = nullptr;
+        int st = gp_create(&q.p, b->stream, &h);
+        if (st == GP_ERR_OOM) break;  // the device is fuller than the accounting: wait for retirements
+        b->queue.pop_front();
+        if (st != GP_OK) {
+            q.state = GP_REQ_FAILED;
+            continue;
+        }
+        if (gp_init_gaussian(h, q.r.frac, q.r.seed, q.r.phase_noise) != GP_OK || ensure_coef(h, GP_IMAG) != GP_OK) {
+            gp_destroy(h);
+            q.state = GP_REQ_FAILED;
+            continue;
+        }
+        q.h = h;
+        q.state = GP_REQ_RUNNING;
+        b->used_bytes += q.bytes;
+    }
+    return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t gp_request_bytes(const gp_params* params, int policy)
+{
+    if (!params || validate(params) != GP_OK) return 0;
+    gp_params p = *params;
+    p.precision = policy_precision(policy);
+    return handle_bytes(p);
+}
+
+int gp_batch_create(size_t max_device_bytes, int check_every, void* cuda_stream, gp_batch** out)
+{
+    if (!out || max_device_bytes == 0 || check_every <= 0) return GP_ERR_ARG;
+    *out = nullptr;
+    gp_batch* b = new (std::nothrow) gp_batch();
+    if (!b) return GP_ERR_OOM;
+    b->max_bytes = max_device_bytes;
+    b->check_every = check_every;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return GP_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    if (cudaMalloc(&b->counts, 8 * sizeof(int)) != cudaSuccess || cudaMalloc(&b->flag, sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(b->flag, 0, sizeof(int), b->stream) != cudaSuccess) {
+        gp_batch_destroy(b);
+        return GP_ERR_OOM;
+    }
+    *out = b;
+    return GP_OK;
+}
+
+void gp_batch_destroy(gp_batch* b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (auto& kv : b->reqs)
+        if (kv.second.h) gp_destroy(kv.second.h);
+    b->g64.release();
+    b->g32.release();
+    cudaFree(b->counts);
+    cudaFree(b->flag);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req, long long* id_out)
+{
+    if (!b || !params || !req || !id_out) return GP_ERR_ARG;
+    int st = validate(params);
+    if (st) return st;
+    if (req->policy != GP_POLICY_FP64 && req->policy != GP_POLICY_FP32_REFINE) return GP_ERR_ARG;
+    if (!(req->tol > 0) || req->cap <= 0 || !std::isfinite(req->phase_noise)) return GP_ERR_ARG;
+    Request q;
+    q.id = b->next_id++;
+    q.p = *params;
+    q.p.precision = policy_precision(req->policy);
+    q.r = *req;
+    q.bytes = handle_bytes(q.p);
+    b->reqs[q.id] = q;
+    b->queue.push_back(q.id);
+    *id_out = q.id;
+    return GP_OK;
+}
+
+int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
+{
+    if (!b) return GP_ERR_ARG;
+    int st = admit(b);
+    if (st) return st;
+    b->g64.clear();
+    b->g32.clear();
+    std::vector<Request*> run;
+    for (auto& kv : b->reqs) {
+        Request& q = kv.second;
+        if (q.state != GP_REQ_RUNNING) continue;
+        const CoefSet& cs = q.h->coef[GP_IMAG];
+        if (q.h->active == GP_FP32_MIXED) {
+            add_instance(b->g32, q.h, pass_args_f32(q.h, cs, 0), pass_args_f32(q.h, cs, 1));
+        } else {
+            add_instance(b->g64, q.h, pass_args(q.h, cs, 0), pass_args(q.h, cs, 1));
+        }
+        run.push_back(&q);
+    }
+    const int k = b->check_every;
+    if (!run.empty()) {
+        if ((st = upload_and_run(b, b->g64, b->counts, k))) return st;
+        if ((st = upload_and_run(b, b->g32, b->counts + 4, k))) return st;
+        BK(cudaStreamSynchronize(b->stream));
+    }
+    // convergence checks between ticks
+    for (Request* q : run) {
+        q->h->scale_pending = true;
+        q->h->steps += k;
+        q->steps += k;
+        gp_obs o;
+        int ost = gp_observables(q->h, &o);
+        q->obs = o;
+        if (ost != GP_OK) {
+            retire(b, *q, GP_REQ_FAILED);
+            continue;
+        }
+        const double de = q->have_e ? std::fabs(o.energy - q->e_last) : INFINITY;
+        q->have_e = true;
+        q->e_last = o.energy;
+        if (q->h->active == GP_FP32_MIXED) {
+            // FP32 phase: hand over to FP64 once the energy has settled to the FP32 level
+            if (de <= q->r.tol32 * std::fabs(o.energy) || q->steps >= q->r.cap) {
+                if (gp_refine_fp64(q->h, 0, GP_IMAG) != GP_OK) {
+                    retire(b, *q, GP_REQ_FAILED);
+                    continue;
+                }
+                q->have_e = false;  // restart the |dE| test in FP64
+            }
+            if (q->steps < q->r.cap) continue;
+        }
+        if (de < q->r.tol || q->steps >= q->r.cap) retire(b, *q, GP_REQ_DONE);
+    }
+    st = admit(b);  // memory freed by retirements
+    if (n_running || n_queued) {
+        int nr = 0;
+        for (auto& kv : b->reqs) nr += kv.second.state == GP_REQ_RUNNING;
+        if (n_running) *n_running = nr;
+        if (n_queued) *n_queued = (int)b->queue.size();
+    }
+    return st;
+}
+
+int gp_batch_poll(gp_batch* b, long long id, int* state, long long* steps, gp_obs* obs, double* psi_out, int release)
+{
+    if (!b) return GP_ERR_ARG;
+    auto it = b->reqs.find(id);
+    if (it == b->reqs.end()) {
+        if (state) *state = GP_REQ_UNKNOWN;
+        return GP_ERR_ARG;
+    }
+    Request& q = it->second;
+    if (state) *state = q.state;
+    if (steps) *steps = q.steps;
+    if (obs) *obs = q.obs;
+    if (q.state == GP_REQ_DONE && psi_out && !q.psi.empty())
+        std::copy(q.psi.begin(), q.psi.end(), psi_out);
+    if (release && (q.state == GP_REQ_DONE || q.state == GP_REQ_FAILED)) b->reqs.erase(it);
+    return GP_OK;
+}
+
+}  // extern "C"

@@ -18,54 +18,7 @@
 
 using namespace gpspin;
 
-namespace {
-
-constexpr int kNormBlocksMax = 4096;
-
-// Coefficient tables and tilings of one mode (imaginary or real time).
-struct CoefSet {
-    bool valid = false;
-    gp_params key{};
-    LineCoef* cx = nullptr;   // [ny][3] x-pass lines (rows), FP64
-    LineCoef* cy = nullptr;   // [nx][3] y-pass lines (columns), FP64
-    double2* ex = nullptr;    // [nx]
-    double2* ey = nullptr;    // [ny]
-    LineCoefF* fx = nullptr;  // complex64 copies (FP32-storage handles only)
-    LineCoefF* fy = nullptr;
-    float2* fex = nullptr;
-    float2* fey = nullptr;
-    LineTiling tx{}, ty{}, ftx{}, fty{};
-};
-
-bool same_physics(const gp_params& a, const gp_params& b)
-{
-    return a.dt == b.dt && a.wx == b.wx && a.wy == b.wy && a.omeg == b.omeg && a.so_type == b.so_type &&
-           a.gamma == b.gamma && a.nx == b.nx && a.ny == b.ny && a.xlen == b.xlen && a.ylen == b.ylen;
-}
-
-}  // namespace
-
-struct gp_handle {
-    gp_params p{};
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int device = 0;
-    int active = GP_FP64;      // precision of the propagated copy
-    double2* psi = nullptr;    // [3][ny][nx] complex128 state (authoritative when active == GP_FP64)
-    double2* work = nullptr;   // [3][nx][ny] transposed intermediate / staging
-    float2* psi32 = nullptr;   // complex64 state (authoritative when active == GP_FP32_MIXED)
-    float2* work32 = nullptr;
-    double* partials = nullptr;
-    double* obs_part = nullptr;
-    double* scal = nullptr;    // [0] pending normalisation, [1] last norm, [2] the constant 1
-    double* obs_out = nullptr; // [8]
-    int* flag = nullptr;       // bit0 coefficient convergence, bit1 norm, bit2 observables
-    CoefSet coef[2];           // per mode
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // gp_profile_step
-    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [precision][mode]
-    bool scale_pending = false;
-    long long steps = 0;
-};
+#include "gp_handle.cuh"
 
 namespace gpspin {
 
@@ -162,10 +115,6 @@ int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32)
     return GP_OK;
 }
 
-}  // namespace gpspin
-
-namespace {
-
 #define CK(x)                                                  \
     do {                                                       \
         if (report_cuda((x), #x) != 0) return GP_ERR_CUDA;     \
@@ -199,6 +148,12 @@ void free_coef(CoefSet& c)
 }
 
 bool wants_fp32(const gp_handle* h) { return h->p.precision == GP_FP32_MIXED; }
+
+bool same_physics(const gp_params& a, const gp_params& b)
+{
+    return a.dt == b.dt && a.wx == b.wx && a.wy == b.wy && a.omeg == b.omeg && a.so_type == b.so_type &&
+           a.gamma == b.gamma && a.nx == b.nx && a.ny == b.ny && a.xlen == b.xlen && a.ylen == b.ylen;
+}
 
 int ensure_coef(gp_handle* h, int mode)
 {
@@ -372,6 +327,16 @@ int sync_status(gp_handle* h)
 
 int y_blocks(const LineTiling& t) { return (t.nlines + t.R - 1) / t.R; }
 
+size_t handle_bytes(const gp_params& p)
+{
+    const size_t n = 3 * (size_t)p.nx * p.ny, lines = (size_t)p.nx + p.ny;
+    size_t b = n * 2 * sizeof(double2);  // psi, work
+    b += kNormBlocksMax * sizeof(double) + (size_t)obs_blocks(p.nx, p.ny) * obs_slots() * sizeof(double);
+    b += 3 * lines * sizeof(LineCoef) + lines * sizeof(double2);  // tables of one mode
+    if (p.precision == GP_FP32_MIXED) b += n * 2 * sizeof(float2) + 3 * lines * sizeof(LineCoefF) + lines * sizeof(float2);
+    return b + 4096;  // scalars, flag and allocation rounding
+}
+
 // Launch sequence of n steps (x-pass, y-pass and, in imaginary time, the
 // normalisation) on the handle's stream.
 template <typename A>
@@ -417,6 +382,10 @@ int run_steps(gp_handle* h, int mode, const A& ax, const A& ay, int gy, long lon
     return enqueue_steps(h, mode, ax, ay, gy, n);
 }
 
+}  // namespace gpspin
+
+namespace {
+
 int propagate_active(gp_handle* h, long long nsteps, int mode)
 {
     int st = ensure_coef(h, mode);
@@ -456,6 +425,7 @@ const char* gp_strerror(int s)
     case GP_ERR_NONFINITE: return "non-finite values in the wave function";
     case GP_ERR_UNSUPPORTED: return "parameters outside the supported range of the tabulated line solver";
     case GP_ERR_TOO_LARGE: return "grid larger than the fixed scratch of gp_propagate_noalloc (nx, ny <= 256)";
+    case GP_ERR_TIMEOUT: return "a device-side wait gave up (bulk copy did not complete)";
     default: return "unknown status";
     }
 }

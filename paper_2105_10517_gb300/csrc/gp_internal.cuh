@@ -110,10 +110,26 @@ int launch_xpass(const PassArgs& a, int mode, cudaStream_t st);
 int launch_ypass(const PassArgs& a, int mode, cudaStream_t st);
 int launch_xpass(const PassArgsF& a, int mode, cudaStream_t st);
 int launch_ypass(const PassArgsF& a, int mode, cudaStream_t st);
+int launch_xpass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st);
+int launch_ypass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st);
+int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st);
+int launch_ypass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st);
 // launchers (gp_reduce.cu)
 int launch_norm(const double2* psi, size_t n, double* partials, int nblk, double da, double* scale, int* flag,
                 cudaStream_t st);
 int launch_finalize_norm(const double* partials, int n, double da, double* scale, int* flag, cudaStream_t st);
+// One CTA per instance: fin[b] = {partials, n_partials, da, scale} of instance b.
+struct FinArgs {
+    const double* partials;
+    int n;
+    double da;
+    double* scale;
+};
+int launch_finalize_norm_batched(const FinArgs* fin, const int* n_inst, int capacity, int* flag, cudaStream_t st);
 int launch_apply_scale(double2* psi, size_t n, double* scale, cudaStream_t st);
 int launch_apply_scale(float2* psi, size_t n, double* scale, cudaStream_t st);
 int launch_set_scalar(double* p, double v, cudaStream_t st);

@@ -103,6 +103,29 @@ __global__ void narrow_kernel(float2* dst, const double2* src, size_t n)
 
 __global__ void set_scalar_kernel(double* p, double v) { *p = v; }
 
+// Batched normalisation: CTA b finalises instance b (same arithmetic and order
+// as finalize_norm_kernel, so an instance gets the same scale alone or batched).
+__global__ void __launch_bounds__(kRedThreads) finalize_norm_batched_kernel(const FinArgs* fin, const int* n_inst,
+                                                                            int* flag)
+{
+    __shared__ double sh[32];
+    if ((int)blockIdx.x >= *n_inst) return;
+    const FinArgs f = fin[blockIdx.x];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < f.n; k += kRedThreads) acc += f.partials[k];
+    double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        double nrm = t * f.da;
+        f.scale[1] = nrm;
+        if (nrm > 0.0 && isfinite(nrm)) {
+            f.scale[0] = 1.0 / sqrt(nrm);
+        } else {
+            f.scale[0] = 1.0;
+            atomicOr(flag, 2);
+        }
+    }
+}
+
 // --------------------------------------------------------- initial state ---
 // splitmix64 (Steele, Lea and Flood, OOPSLA 2014) on the counter seed ^ index.
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
@@ -274,6 +297,13 @@ int launch_norm(const double2* psi, size_t n, double* partials, int nblk, double
 int launch_finalize_norm(const double* partials, int n, double da, double* scale, int* flag, cudaStream_t st)
 {
     finalize_norm_kernel<<<1, kRedThreads, 0, st>>>(partials, n, da, scale, flag);
+    return report_cuda(cudaGetLastError(), __func__);
+}
+
+int launch_finalize_norm_batched(const FinArgs* fin, const int* n_inst, int capacity, int* flag, cudaStream_t st)
+{
+    if (capacity <= 0) return 0;
+    finalize_norm_batched_kernel<<<capacity, kRedThreads, 0, st>>>(fin, n_inst, flag);
     return report_cuda(cudaGetLastError(), __func__);
 }
 

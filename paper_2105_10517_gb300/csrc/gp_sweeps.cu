@@ -479,18 +479,17 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
 __device__ __forceinline__ int sidx(const LineTiling& T, int lc, int k) { return lc * T.Lp + k + k / T.m; }
 
 // --------------------------------------------------------------- x-pass ----
+// One CTA of the x-pass: lines cta*R .. cta*R + R - 1 of instance A.
 template <int MODE, typename C>
-__global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
+__device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar)
 {
     typedef typename RealOf<C>::type R;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t mbar;
     const LineTiling& T = A.t;
     C* sa = reinterpret_cast<C*>(smem_raw);
     C* sb = reinterpret_cast<C*>(smem_raw + T.off_b);
     C* cf = reinterpret_cast<C*>(smem_raw + T.off_cf);
     C* cb = reinterpret_cast<C*>(smem_raw + T.off_cb);
-    const int line0 = blockIdx.x * T.R;
+    const int line0 = cta * T.R;
     const int nl = min(T.R, T.nlines - line0);
     const int nx = A.nx, ny = A.ny, L = T.L;
     const size_t plane = (size_t)nx * ny;
@@ -503,7 +502,7 @@ __global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
     k.dtc2 = R(A.dt * A.c2 * s * s);
     k.dtr = R(A.dt * A.rabi * 0.70710678118654752440);
     k.s = R(s);
-    for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * L; e += T.threads) {
         int r = e / L, i = e - r * L, j = line0 + r;
         C a, b, c;
         if (T.bulk) {
@@ -535,7 +534,7 @@ __global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
     __syncthreads();
     if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, nl);
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
-    for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * L; e += T.threads) {
         int i = e / nl, r = e - i * nl, j = line0 + r;
         C xp, x0, xm;
         sigma_y_to_x(sa[sidx(T, r * 3 + 0, i)], sa[sidx(T, r * 3 + 1, i)], sa[sidx(T, r * 3 + 2, i)], xp, x0, xm);
@@ -546,29 +545,48 @@ __global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
     }
 }
 
+template <int MODE, typename C>
+__global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    xpass_body<MODE, C>(A, blockIdx.x, smem_raw, mbar);
+}
+
+// Many instances in one launch: CTA b works on item items[b] = (instance, cta)
+// for b < *n_items (the launch may be larger than the current item count).
+template <int MODE, typename C>
+__global__ void __launch_bounds__(512) xpass_batched(const PassArgsT<C>* args, const int2* items, const int* n_items)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    if ((int)blockIdx.x >= *n_items) return;
+    const int2 it = items[blockIdx.x];
+    const PassArgsT<C> A = args[it.x];
+    xpass_body<MODE, C>(A, it.y, smem_raw, mbar);
+}
+
 // --------------------------------------------------------------- y-pass ----
 // Partial norms: each thread sums its sites' |psi|^2 in the pass's precision
 // (a few dozen sites), the CTA then adds the threads' sums in FP64.
 template <int MODE, typename C>
-__global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
+__device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar,
+                                           double* wsum)
 {
     typedef typename RealOf<C>::type R;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t mbar;
-    __shared__ double wsum[32];
     const LineTiling& T = A.t;
     C* sa = reinterpret_cast<C*>(smem_raw);
     C* sb = reinterpret_cast<C*>(smem_raw + T.off_b);
     C* cf = reinterpret_cast<C*>(smem_raw + T.off_cf);
     C* cb = reinterpret_cast<C*>(smem_raw + T.off_cb);
-    const int line0 = blockIdx.x * T.R;
+    const int line0 = cta * T.R;
     const int nl = min(T.R, T.nlines - line0);
     const int nx = A.nx, ny = A.ny, L = T.L;
     const size_t plane = (size_t)nx * ny;
     // stage the CTA's rows t[mu][i][*] into sb (contiguous [r][mu][j])
     if (T.bulk && !stage_rows(sb, A.in, plane, line0, nl, L, &mbar, A.err)) return;
 
-    for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * L; e += T.threads) {
         int r = e / L, j = e - r * L, i = line0 + r;
         if (T.bulk) {
             const C* row = sb + (size_t)r * 3 * L + j;
@@ -585,7 +603,7 @@ __global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
     __syncthreads();
     if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, nl);
     R acc = R(0);
-    for (int e = threadIdx.x; e < nl * L; e += blockDim.x) {
+    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * L; e += T.threads) {
         int j = e / nl, r = e - j * nl, i = line0 + r;
         C a, b, c;
         from_sigma_x(sa[sidx(T, r * 3 + 0, j)], sa[sidx(T, r * 3 + 1, j)], sa[sidx(T, r * 3 + 2, j)], a, b, c);
@@ -598,15 +616,38 @@ __global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
     if (A.partials) {
         double dacc = (double)acc;
         for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
+        // threads past T.threads (batched launches) hold acc = 0: the sum is the
+        // same as in a launch of exactly T.threads threads
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
         if (lane == 0) wsum[warp] = dacc;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int w = 0; w < nw; ++w) t += wsum[w];
-            A.partials[blockIdx.x] = t;
+            A.partials[cta] = t;
         }
     }
+}
+
+template <int MODE, typename C>
+__global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    __shared__ double wsum[32];
+    ypass_body<MODE, C>(A, blockIdx.x, smem_raw, mbar, wsum);
+}
+
+template <int MODE, typename C>
+__global__ void __launch_bounds__(512) ypass_batched(const PassArgsT<C>* args, const int2* items, const int* n_items)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    __shared__ double wsum[32];
+    if ((int)blockIdx.x >= *n_items) return;
+    const int2 it = items[blockIdx.x];
+    const PassArgsT<C> A = args[it.x];
+    ypass_body<MODE, C>(A, it.y, smem_raw, mbar, wsum);
 }
 
 // ------------------------------------------------------------- launchers ---
@@ -676,6 +717,49 @@ int launch_xpass(const PassArgsF& a, int mode, cudaStream_t st)
 int launch_ypass(const PassArgsF& a, int mode, cudaStream_t st)
 {
     return mode == 1 ? launch_pass(ypass_kernel<1, float2>, a, st) : launch_pass(ypass_kernel<0, float2>, a, st);
+}
+
+// Batched launches: grid = capacity items (CTAs past *n_items exit at once),
+// threads and dynamic shared memory the maximum over the batch's instances.
+template <typename C, typename K>
+static int launch_batched_t(K kernel, const PassArgsT<C>* args, const int2* items, const int* n_items, int capacity,
+                            int threads, size_t smem, cudaStream_t st)
+{
+    if (capacity <= 0) return 0;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return report_cuda(e, "cudaFuncSetAttribute(batched pass)");
+    }
+    kernel<<<capacity, threads, smem, st>>>(args, items, n_items);
+    return report_cuda(cudaGetLastError(), "batched pass launch");
+}
+
+int launch_xpass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st)
+{
+    return mode == 1 ? launch_batched_t(xpass_batched<1, double2>, args, items, n_items, capacity, threads, smem, st)
+                     : launch_batched_t(xpass_batched<0, double2>, args, items, n_items, capacity, threads, smem, st);
+}
+
+int launch_ypass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st)
+{
+    return mode == 1 ? launch_batched_t(ypass_batched<1, double2>, args, items, n_items, capacity, threads, smem, st)
+                     : launch_batched_t(ypass_batched<0, double2>, args, items, n_items, capacity, threads, smem, st);
+}
+
+int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st)
+{
+    return mode == 1 ? launch_batched_t(xpass_batched<1, float2>, args, items, n_items, capacity, threads, smem, st)
+                     : launch_batched_t(xpass_batched<0, float2>, args, items, n_items, capacity, threads, smem, st);
+}
+
+int launch_ypass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st)
+{
+    return mode == 1 ? launch_batched_t(ypass_batched<1, float2>, args, items, n_items, capacity, threads, smem, st)
+                     : launch_batched_t(ypass_batched<0, float2>, args, items, n_items, capacity, threads, smem, st);
 }
 
 }  // namespace gpspin

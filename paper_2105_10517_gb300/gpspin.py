@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB_PATH = os.path.join(PKG, "libgpspin.so")
 BUILD_DIR = os.path.join(PKG, "_build")
-SOURCES = ["gp_capi.cu", "gp_sweeps.cu", "gp_reduce.cu", "gp_noalloc.cu"]
+SOURCES = ["gp_capi.cu", "gp_sweeps.cu", "gp_reduce.cu", "gp_noalloc.cu", "gp_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
 
@@ -28,13 +28,13 @@ FP64, FP32_MIXED = 0, 1
 SUB_P, SUB_X, SUB_Y = 0, 1, 2
 
 STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP_ERR_NONFINITE",
-          5: "GP_ERR_UNSUPPORTED", 6: "GP_ERR_TOO_LARGE"}
+          5: "GP_ERR_UNSUPPORTED", 6: "GP_ERR_TOO_LARGE", 7: "GP_ERR_TIMEOUT"}
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
            "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step",
-           "gp_propagate_noalloc",
-           "gp_strerror"]
+           "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
+           "gp_batch_step", "gp_batch_poll", "gp_strerror"]
 
 
 def _nvcc():
@@ -53,6 +53,7 @@ def build(force=False, verbose=False):
     """Compile the CUDA sources (in parallel, one -gencode for sm_103a) and link
     libgpspin.so next to this file.  Returns the library path."""
     deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "gp_internal.cuh"),
+                                                        os.path.join(CSRC, "gp_handle.cuh"),
                                                         os.path.join(ROOT, "include", "gpspin.h")]
     if not force and not _stale(LIB_PATH, deps):
         return LIB_PATH
@@ -103,6 +104,21 @@ class Obs(ctypes.Structure):
     ]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("frac", ctypes.c_double * 3),
+        ("seed", ctypes.c_ulonglong),
+        ("phase_noise", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("tol32", ctypes.c_double),
+        ("cap", ctypes.c_longlong),
+        ("policy", ctypes.c_int),
+    ]
+
+
+POLICY_FP64, POLICY_FP32_REFINE = 0, 1
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_UNKNOWN = 0, 1, 2, 3, 4
+
 _lib = None
 
 
@@ -130,6 +146,17 @@ def load():
     lib.gp_profile_step.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_float)]
     lib.gp_propagate_noalloc.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_longlong, ip, vp]
     lib.gp_propagate_noalloc.restype = ctypes.c_int
+    lib.gp_request_bytes.argtypes = [ctypes.POINTER(Params), ip]
+    lib.gp_request_bytes.restype = ctypes.c_size_t
+    lib.gp_batch_create.argtypes = [ctypes.c_size_t, ip, vp, ctypes.POINTER(vp)]
+    lib.gp_batch_destroy.argtypes = [vp]
+    lib.gp_batch_destroy.restype = None
+    lib.gp_batch_submit.argtypes = [vp, ctypes.POINTER(Params), ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_longlong)]
+    lib.gp_batch_step.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.gp_batch_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(Obs), dp, ip]
+    for name in ("gp_batch_create", "gp_batch_submit", "gp_batch_step", "gp_batch_poll"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.gp_strerror.argtypes = [ip]
     lib.gp_strerror.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
@@ -265,3 +292,66 @@ class Solver:
         _check(load().gp_observables(self._h, ctypes.byref(o)), "gp_observables")
         return dict(norm=np.array(o.norm[:]), norm_total=o.norm_total, magnetization=o.magnetization,
                     energy=o.energy, mu=o.mu, steps=o.steps)
+
+
+def request_bytes(params, policy=POLICY_FP64):
+    return int(load().gp_request_bytes(ctypes.byref(make_params(params)), int(policy)))
+
+
+class Batch:
+    """A gp_batch: continuously batched imaginary-time solves on the current device."""
+
+    def __init__(self, max_bytes, check_every=100, stream=None):
+        lib = load()
+        b = ctypes.c_void_p()
+        s = ctypes.c_void_p(int(stream)) if stream is not None else None
+        _check(lib.gp_batch_create(ctypes.c_size_t(int(max_bytes)), int(check_every), s, ctypes.byref(b)),
+               "gp_batch_create")
+        self._b = b
+        self.check_every = check_every
+        self._shape = {}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().gp_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, params, frac=(0.25, 0.5, 0.25), seed=1, phase_noise=1e-3, tol=1e-9, tol32=1e-7, cap=20000,
+               policy=POLICY_FP64):
+        r = Request((ctypes.c_double * 3)(*frac), int(seed), float(phase_noise), float(tol), float(tol32), int(cap),
+                    int(policy))
+        rid = ctypes.c_longlong()
+        _check(load().gp_batch_submit(self._b, ctypes.byref(make_params(params)), ctypes.byref(r), ctypes.byref(rid)),
+               "gp_batch_submit")
+        self._shape[rid.value] = (3, int(params["ny"]), int(params["nx"]))
+        return rid.value
+
+    def step(self):
+        nr, nq = ctypes.c_int(), ctypes.c_int()
+        _check(load().gp_batch_step(self._b, ctypes.byref(nr), ctypes.byref(nq)), "gp_batch_step")
+        return nr.value, nq.value
+
+    def poll(self, rid, fetch=False, release=False):
+        """(state, steps, observables dict, psi or None)."""
+        st, steps, o = ctypes.c_int(), ctypes.c_longlong(), Obs()
+        psi = np.empty(self._shape[rid], dtype=np.complex128) if fetch else None
+        ptr = _dptr(psi) if fetch else None
+        _check(load().gp_batch_poll(self._b, int(rid), ctypes.byref(st), ctypes.byref(steps), ctypes.byref(o), ptr,
+                                    int(bool(release))), "gp_batch_poll")
+        obs = dict(norm=np.array(o.norm[:]), norm_total=o.norm_total, magnetization=o.magnetization,
+                   energy=o.energy, mu=o.mu, steps=o.steps)
+        if fetch and st.value != REQ_DONE:
+            psi = None
+        return st.value, steps.value, obs, psi
