@@ -71,6 +71,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, help="vortex512 (default), quench1024 or precision2048")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving benchmark: the seeded request trace through the batched server and one at a time")
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--cap", type=int, default=20000)
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--no-plain", action="store_true", help="serving: skip the one-at-a-time FP64 baseline")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="storage precision (default: fp64; precision2048 defaults to fp32)")
     return ap.parse_args()
@@ -356,8 +363,60 @@ def run_reference(args):
     }
 
 
+def run_serving(args):
+    """Parameter-sweep serving: continuous batching (FP32 storage then FP64
+    refinement, and FP64 throughout) against the plain one-at-a-time FP64 path
+    on the same seeded trace; solves/s, p50/p99 arrival-to-converged latency and
+    the energy agreement of every served result with the plain FP64 result."""
+    import numpy as np
+    import torch
+    from paper_2105_10517_gb300 import gpspin, inputs, serve
+    gpspin.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    trace = inputs.serving_trace(n=args.requests, rate=args.rate, seed=4)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.8)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    mixed, rm = serve.serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=budget, cap=args.cap,
+                                    tol=args.tol)
+    b64, rb = serve.serve_batched(trace, policy=gpspin.POLICY_FP64, max_bytes=budget, cap=args.cap, tol=args.tol)
+    if args.no_plain:  # batched FP64 equals the plain path to rounding (tested): use it as the reference
+        plain, rp = dict(b64, note="not run; batched FP64 used as the reference"), rb
+    else:
+        plain, rp = serve.serve_one_at_a_time(trace, cap=args.cap, tol=args.tol)
+    clocks.stop()
+
+    def agreement(ra):
+        ref = {r["arrival"]: r for r in rp}
+        d_conv, d_cap = [], []
+        for r in ra:
+            q = ref[r["arrival"]]
+            d = abs(r["energy"] - q["energy"]) / abs(q["energy"])
+            (d_cap if (r["steps"] >= args.cap or q["steps"] >= args.cap) else d_conv).append(d)
+        f = lambda v: {"n": len(v), "max_rel_dE": max(v) if v else None,
+                       "frac_within_1e-6": (sum(x <= 1e-6 for x in v) / len(v)) if v else None}
+        return {"converged": f(d_conv), "capped": f(d_cap)}
+
+    return {
+        "metric": METRIC, "mode": "serving", "value": mixed["solves_per_s"], "unit": "solves/s",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "f32 storage + f64 refinement",
+        "data": f"synthetic request trace: {args.requests} requests, Poisson arrivals at {args.rate}/s (seed 4), "
+                f"N in {{128,256,384,512}}, DX=32/N, DT=0.1 DX^2, imaginary time to |dE|<{args.tol:g} per 100 "
+                f"steps, cap {args.cap}",
+        "batched_mixed": mixed, "batched_fp64": b64, "plain_fp64_one_at_a_time": plain,
+        "speedup_solves_per_s_vs_plain": mixed["solves_per_s"] / plain["solves_per_s"],
+        "speedup_fp64_batched_vs_plain": b64["solves_per_s"] / plain["solves_per_s"],
+        "energy_agreement_vs_plain_fp64": {"batched_mixed": agreement(rm), "batched_fp64": agreement(rb)},
+        "device_budget_bytes": budget, "clocks": clocks.summary(),
+    }
+
+
 def main():
     args = parse()
+    if args.serve:
+        print(json.dumps(run_serving(args)))
+        return
     if args.impl == "reference":
         out = run_reference(args)
         if out:

@@ -182,6 +182,7 @@ typedef struct {
     double tol32;             /* GP_POLICY_FP32_REFINE: leave FP32 when |dE| <= tol32 |E|     */
     long long cap;            /* step cap (a capped solve is reported as done)               */
     int policy;               /* gp_policy: FP64 throughout, or FP32 then FP64 refinement    */
+    long long refine_steps;   /* GP_POLICY_FP32_REFINE: FP64 from cap - refine_steps at the latest */
 } gp_request;
 
 /* Device bytes one solve with these parameters and policy occupies. */

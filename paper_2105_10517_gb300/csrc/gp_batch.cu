@@ -258,7 +258,8 @@ int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req,
     int st = validate(params);
     if (st) return st;
     if (req->policy != GP_POLICY_FP64 && req->policy != GP_POLICY_FP32_REFINE) return GP_ERR_ARG;
-    if (!(req->tol > 0) || req->cap <= 0 || !std::isfinite(req->phase_noise)) return GP_ERR_ARG;
+    if (!(req->tol > 0) || req->cap <= 0 || req->refine_steps < 0 || !std::isfinite(req->phase_noise))
+        return GP_ERR_ARG;
     Request q;
     q.id = b->next_id++;
     q.p = *params;
@@ -312,8 +313,9 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
         q->have_e = true;
         q->e_last = o.energy;
         if (q->h->active == GP_FP32_MIXED) {
-            // FP32 phase: hand over to FP64 once the energy has settled to the FP32 level
-            if (de <= q->r.tol32 * std::fabs(o.energy) || q->steps >= q->r.cap) {
+            // FP32 phase: hand over to FP64 once the energy has settled to the FP32
+            // level, and in any case early enough for a final FP64 refinement block
+            if (de <= q->r.tol32 * std::fabs(o.energy) || q->steps + q->r.refine_steps >= q->r.cap) {
                 if (gp_refine_fp64(q->h, 0, GP_IMAG) != GP_OK) {
                     retire(b, *q, GP_REQ_FAILED);
                     continue;

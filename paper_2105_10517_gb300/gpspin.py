@@ -113,6 +113,7 @@ class Request(ctypes.Structure):
         ("tol32", ctypes.c_double),
         ("cap", ctypes.c_longlong),
         ("policy", ctypes.c_int),
+        ("refine_steps", ctypes.c_longlong),
     ]
 
 
@@ -329,9 +330,9 @@ class Batch:
         self.close()
 
     def submit(self, params, frac=(0.25, 0.5, 0.25), seed=1, phase_noise=1e-3, tol=1e-9, tol32=1e-7, cap=20000,
-               policy=POLICY_FP64):
+               policy=POLICY_FP64, refine_steps=2000):
         r = Request((ctypes.c_double * 3)(*frac), int(seed), float(phase_noise), float(tol), float(tol32), int(cap),
-                    int(policy))
+                    int(policy), int(refine_steps))
         rid = ctypes.c_longlong()
         _check(load().gp_batch_submit(self._b, ctypes.byref(make_params(params)), ctypes.byref(r), ctypes.byref(rid)),
                "gp_batch_submit")

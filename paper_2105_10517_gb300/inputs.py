@@ -73,3 +73,26 @@ CONFIGS = {
 def physics(cfg):
     """The parameter keys of a workload, without its run-control keys."""
     return {k: v for k, v in cfg.items() if k not in ("mode", "steps", "seed")}
+
+
+def serving_trace(n=256, rate=20.0, seed=4, sizes=(128, 256, 384, 512), box=32.0):
+    """Seeded request trace of the parameter-sweep serving workload: Poisson
+    arrivals at `rate` per second; grids drawn uniformly from `sizes` on a box of
+    side `box` (DX = box/N) with the imaginary-time step DT = 0.1 DX^2; Omega ~
+    U[0, 0.9], gamma ~ U[0, 2] (Rashba or Dresselhaus 50/50), R ~ U[0, 1],
+    c0 ~ U[100, 800], c2 ~ U[-20, 20]; each request starts from the seeded
+    Gaussian state with its own seed."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    out = []
+    for k in range(n):
+        nx = int(rng.choice(sizes))
+        dx = box / nx
+        out.append(dict(
+            arrival=float(t[k]),
+            params=dict(nx=nx, ny=nx, xlen=box, ylen=box, dt=0.1 * dx * dx, omeg=float(rng.uniform(0, 0.9)),
+                        gamma=float(rng.uniform(0, 2)), so_type=int(rng.integers(1, 3)),
+                        rabi=float(rng.uniform(0, 1)), c0=float(rng.uniform(100, 800)),
+                        c2=float(rng.uniform(-20, 20))),
+            seed=1000 + k))
+    return out
