@@ -111,6 +111,13 @@ int gp_get_state(gp_handle* h, double* psi_out);
  * splitmix64(seed ^ ((c ny + j) nx + i)) times 2^-53; then normalised to 1. */
 int gp_init_gaussian(gp_handle* h, const double frac[3], unsigned long long seed, double phase_noise);
 
+/* The same initial state with centre vortices built in (the SO-coupled states
+ * described after Fig. S1: (-+1, 0, +-1) antiferromagnetic, (0, +-1, +-2)
+ * ferromagnetic): component c is multiplied by (x + i sgn(l_c) y)^|l_c| before
+ * normalisation, winding[c] = l_c in [-8, 8]. */
+int gp_init_winding(gp_handle* h, const double frac[3], const int winding[3], unsigned long long seed,
+                    double phase_noise);
+
 /* Advances h by nsteps split-step Crank-Nicolson steps: P(dt) -> X(dt) -> Y(dt),
  * and in imaginary time (mode GP_IMAG) renormalisation to a total norm of 1
  * after every step.  mode GP_REAL propagates i d_t psi = H psi.  nsteps = 0 is

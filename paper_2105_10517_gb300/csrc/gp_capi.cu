@@ -395,7 +395,6 @@ int propagate_active(gp_handle* h, long long nsteps, int mode)
     const bool f32 = h->active == GP_FP32_MIXED;
     const int gy = y_blocks(f32 ? cs.fty : cs.ty);
     if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
-    if (mode == GP_IMAG) CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     if (f32) {
         PassArgsF ax = pass_args_f32(h, cs, 0), ay = pass_args_f32(h, cs, 1);
         if (mode == GP_IMAG) ay.partials = h->partials;
@@ -542,12 +541,16 @@ int gp_get_state(gp_handle* h, double* psi_out)
     return sync_status(h);
 }
 
-int gp_init_gaussian(gp_handle* h, const double frac[3], unsigned long long seed, double phase_noise)
+int gp_init_winding(gp_handle* h, const double frac[3], const int winding[3], unsigned long long seed,
+                    double phase_noise)
 {
-    if (!h || !frac || !is_finite(phase_noise)) return GP_ERR_ARG;
-    for (int c = 0; c < 3; ++c)
+    if (!h || !frac || !winding || !is_finite(phase_noise)) return GP_ERR_ARG;
+    for (int c = 0; c < 3; ++c) {
         if (!(frac[c] >= 0) || !is_finite(frac[c])) return GP_ERR_ARG;
-    LK(launch_init_gaussian(h->psi, h->p.nx, h->p.ny, h->p.xlen, h->p.ylen, frac, seed, phase_noise, h->stream));
+        if (winding[c] < -8 || winding[c] > 8) return GP_ERR_ARG;
+    }
+    LK(launch_init_gaussian(h->psi, h->p.nx, h->p.ny, h->p.xlen, h->p.ylen, frac, winding, seed, phase_noise,
+                            h->stream));
     LK(narrow_from_psi(h));
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     LK(launch_norm(h->psi, n_elems(h), h->partials, norm_blocks(h), cell(h), h->scal, h->flag, h->stream));
@@ -558,13 +561,32 @@ int gp_init_gaussian(gp_handle* h, const double frac[3], unsigned long long seed
     return (flag & 2) ? GP_ERR_NONFINITE : GP_OK;
 }
 
+int gp_init_gaussian(gp_handle* h, const double frac[3], unsigned long long seed, double phase_noise)
+{
+    const int none[3] = {0, 0, 0};
+    return gp_init_winding(h, frac, none, seed, phase_noise);
+}
+
+// Status bits the kernels of a propagation set: a bulk-copy wait that gave up
+// (bit 8) or a non-finite norm (bit 2).
+static int check_flags(gp_handle* h)
+{
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (flag & 8) return GP_ERR_TIMEOUT;
+    if (flag & 2) return GP_ERR_NONFINITE;
+    return GP_OK;
+}
+
 int gp_propagate(gp_handle* h, long long nsteps, int mode)
 {
     if (!h || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
     if (nsteps == 0) return GP_OK;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     int st = propagate_active(h, nsteps, mode);
     if (st) return st;
-    return sync_status(h);
+    return check_flags(h);
 }
 
 int gp_refine_fp64(gp_handle* h, long long nsteps, int mode)
@@ -576,9 +598,10 @@ int gp_refine_fp64(gp_handle* h, long long nsteps, int mode)
         h->active = GP_FP64;
     }
     if (nsteps == 0) return sync_status(h);
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     int st = propagate_active(h, nsteps, mode);
     if (st) return st;
-    return sync_status(h);
+    return check_flags(h);
 }
 
 int gp_profile_step(gp_handle* h, int mode, float* ms_out)

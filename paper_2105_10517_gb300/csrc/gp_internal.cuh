@@ -137,7 +137,7 @@ int launch_scaled_copy(double2* dst, const double2* src, size_t n, const double*
 int launch_scaled_copy(double2* dst, const float2* src, size_t n, const double* scale, cudaStream_t st);
 int launch_narrow(float2* dst, const double2* src, size_t n, cudaStream_t st);
 int launch_init_gaussian(double2* psi, int nx, int ny, double xlen, double ylen, const double frac[3],
-                         unsigned long long seed, double noise, cudaStream_t st);
+                         const int winding[3], unsigned long long seed, double noise, cudaStream_t st);
 int obs_blocks(int nx, int ny);
 int obs_slots();
 int launch_observables(const double2* psi, const double* scale, int nx, int ny, double xlen, double ylen, double wx,

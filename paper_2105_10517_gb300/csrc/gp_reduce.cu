@@ -136,8 +136,10 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x)
     return z ^ (z >> 31);
 }
 
+// psi_c = sqrt(f_c) pi^-1/2 (x + i sgn(l_c) y)^|l_c| exp(-(x^2+y^2)/2) exp(i phi),
+// phi = noise (2u - 1), u from splitmix64(seed ^ ((c ny + j) nx + i)).
 __global__ void init_gaussian_kernel(double2* psi, int nx, int ny, double xlen, double ylen, double f0, double f1,
-                                     double f2, unsigned long long seed, double noise)
+                                     double f2, int l0, int l1, int l2, unsigned long long seed, double noise)
 {
     const size_t plane = (size_t)nx * ny;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 3 * plane; k += (size_t)gridDim.x * blockDim.x) {
@@ -149,10 +151,15 @@ __global__ void init_gaussian_kernel(double2* psi, int nx, int ny, double xlen, 
         double u = (double)(splitmix64(seed ^ (unsigned long long)k) >> 11) * 0x1.0p-53;
         double ph = noise * (2.0 * u - 1.0);
         double fr = c == 0 ? f0 : (c == 1 ? f1 : f2);
+        int l = c == 0 ? l0 : (c == 1 ? l1 : l2);
         double amp = sqrt(fr) * exp(-0.5 * (x * x + y * y)) / sqrt(3.14159265358979323846);
         double sn, cs;
         sincos(ph, &sn, &cs);
-        psi[k] = make_double2(amp * cs, amp * sn);
+        double2 v = make_double2(amp * cs, amp * sn);
+        // centre vortex of charge l: multiply by (x + i sgn(l) y)^|l|
+        const double zy = l > 0 ? y : -y;
+        for (int q = 0; q < (l < 0 ? -l : l); ++q) v = make_double2(v.x * x - v.y * zy, v.x * zy + v.y * x);
+        psi[k] = v;
     }
 }
 
@@ -346,11 +353,11 @@ int launch_narrow(float2* dst, const double2* src, size_t n, cudaStream_t st)
 }
 
 int launch_init_gaussian(double2* psi, int nx, int ny, double xlen, double ylen, const double frac[3],
-                         unsigned long long seed, double noise, cudaStream_t st)
+                         const int winding[3], unsigned long long seed, double noise, cudaStream_t st)
 {
     size_t n = 3 * (size_t)nx * ny;
     init_gaussian_kernel<<<grid_for(n, 256, 1216), 256, 0, st>>>(psi, nx, ny, xlen, ylen, frac[0], frac[1], frac[2],
-                                                                 seed, noise);
+                                                                 winding[0], winding[1], winding[2], seed, noise);
     return report_cuda(cudaGetLastError(), __func__);
 }
 

@@ -32,7 +32,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-           "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step",
+           "gp_init_winding", "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_strerror"]
 
@@ -140,6 +140,8 @@ def load():
     lib.gp_set_state.argtypes = [vp, dp, ip]
     lib.gp_get_state.argtypes = [vp, dp]
     lib.gp_init_gaussian.argtypes = [vp, dp, ctypes.c_ulonglong, ctypes.c_double]
+    lib.gp_init_winding.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.c_ulonglong, ctypes.c_double]
+    lib.gp_init_winding.restype = ctypes.c_int
     lib.gp_propagate.argtypes = [vp, ctypes.c_longlong, ip]
     lib.gp_refine_fp64.argtypes = [vp, ctypes.c_longlong, ip]
     lib.gp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
@@ -270,6 +272,11 @@ class Solver:
     def init_gaussian(self, frac=(0.25, 0.5, 0.25), seed=1, phase_noise=1e-3):
         f = np.asarray(frac, dtype=np.float64)
         _check(load().gp_init_gaussian(self._h, _dptr(f), int(seed), float(phase_noise)), "gp_init_gaussian")
+
+    def init_winding(self, frac=(0.25, 0.5, 0.25), winding=(0, 0, 0), seed=1, phase_noise=1e-3):
+        f = np.asarray(frac, dtype=np.float64)
+        w = (ctypes.c_int * 3)(*[int(v) for v in winding])
+        _check(load().gp_init_winding(self._h, _dptr(f), w, int(seed), float(phase_noise)), "gp_init_winding")
 
     def propagate(self, nsteps, mode=IMAG):
         _check(load().gp_propagate(self._h, int(nsteps), int(mode)), "gp_propagate")

@@ -50,6 +50,22 @@ def gaussian_state(nx, ny, xlen, ylen, frac=(0.25, 0.5, 0.25), seed=1, phase_noi
     return psi.astype(np.complex128)
 
 
+def winding_state(nx, ny, xlen, ylen, frac=(0.25, 0.5, 0.25), winding=(0, 0, 0), seed=1, phase_noise=1e-3,
+                  normalize=True):
+    """gaussian_state times (x + i sgn(l_c) y)^|l_c| per component: centre vortices
+    of charge l_c built into the initial guess (normalised to 1)."""
+    x, y = grid(nx, ny, xlen, ylen)
+    psi = gaussian_state(nx, ny, xlen, ylen, frac, seed, phase_noise, normalize=False)
+    X, Y = np.meshgrid(x, y)
+    for c, l in enumerate(winding):
+        if l:
+            psi[c] = psi[c] * (X + 1j * np.sign(l) * Y) ** abs(int(l))
+    if normalize:
+        n = np.sum(np.abs(psi) ** 2) * (xlen / nx) * (ylen / ny)
+        psi = psi / math.sqrt(n)
+    return psi.astype(np.complex128)
+
+
 def random_state(nx, ny, seed=7, scale=1.0):
     """A rough complex field (splitmix64 real and imaginary parts in [-1, 1)) for
     substep tests that must exercise every coefficient, not just smooth data."""
