@@ -340,6 +340,46 @@ int orc_normalize(const orc_params* p, cplx* psi)
     return ORC_OK;
 }
 
+/* ---- magnetisation-constrained normalisation (gamma = R = 0) ---------------- */
+/* Enforces both conditions printed below Eq. (S.5), N = 1 and N_{+1} - N_{-1} = m,
+ * with one factor per component, psi_c <- sigma_c psi_c, and the extra condition
+ * sigma_{+1} sigma_{-1} = sigma_0^2 of the normalised gradient flow for spin-1
+ * condensates (Bao and Lim, SIAM J. Sci. Comput. 30 (2008) 1925).  With
+ * a = sigma_0^2 the conditions give sigma_{+-}^2 = (1 +- m - a N0) / (2 N_{+-}) and
+ * the quadratic (N0^2 - 4 N+ N-) a^2 - 2 N0 a + (1 - m^2) = 0, whose root in
+ * (0, 1/N0] is taken.  An empty +-1 component keeps sigma = 1. */
+int orc_normalize_m(const orc_params* p, cplx* psi, double m)
+{
+    if (!(m > -1.0 && m < 1.0)) return ORC_EARG;
+    const double dA = grid_dx(p) * grid_dy(p);
+    const size_t plane = (size_t)p->nx * p->ny;
+    double nc[3] = { 0, 0, 0 };
+    for (int c = 0; c < 3; ++c)
+        for (size_t k = 0; k < plane; ++k) nc[c] += creal(psi[c * plane + k] * conj(psi[c * plane + k]));
+    for (int c = 0; c < 3; ++c) nc[c] *= dA;
+    double qa = nc[1] * nc[1] - 4.0 * nc[0] * nc[2];
+    double a;
+    if (fabs(qa) < 1e-14 * (nc[1] * nc[1] + 1e-300)) {
+        a = (1.0 - m * m) / (2.0 * nc[1]);
+    } else {
+        double disc = nc[1] * nc[1] - qa * (1.0 - m * m);
+        if (disc < 0) return ORC_EARG;
+        a = (nc[1] - sqrt(disc)) / qa;
+    }
+    if (!(a > 0) || !isfinite(a)) return ORC_EARG;
+    double sig[3];
+    sig[1] = sqrt(a);
+    for (int s = 0; s < 2; ++s) {
+        int c = s == 0 ? 0 : 2;
+        double num = 1.0 + (s == 0 ? m : -m) - a * nc[1];
+        sig[c] = nc[c] > 0 ? sqrt(num / (2.0 * nc[c])) : 1.0;
+        if (!isfinite(sig[c])) return ORC_EARG;
+    }
+    for (int c = 0; c < 3; ++c)
+        for (size_t k = 0; k < plane; ++k) psi[c * plane + k] *= sig[c];
+    return ORC_OK;
+}
+
 /* ---- one full step and propagation ----------------------------------------- */
 int orc_step(const orc_params* p, cplx* psi, int mode)
 {
@@ -349,6 +389,17 @@ int orc_step(const orc_params* p, cplx* psi, int mode)
     if ((st = orc_substep_y(p, psi, mode))) return st;
     if (mode == ORC_IMAG) return orc_normalize(p, psi);
     return ORC_OK;
+}
+
+/* Imaginary-time step with the magnetisation-constrained normalisation. */
+int orc_step_m(const orc_params* p, cplx* psi, double m)
+{
+    int st;
+    if (so_gamma(p) != 0.0 || p->rabi != 0.0) return ORC_EARG;
+    if ((st = orc_substep_p(p, psi, ORC_IMAG))) return st;
+    if ((st = orc_substep_x(p, psi, ORC_IMAG))) return st;
+    if ((st = orc_substep_y(p, psi, ORC_IMAG))) return st;
+    return orc_normalize_m(p, psi, m);
 }
 
 int orc_propagate(const orc_params* p, cplx* psi, long long nsteps, int mode)

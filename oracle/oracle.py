@@ -60,6 +60,10 @@ def _load():
             fn.restype = ctypes.c_int
         lib.orc_propagate.argtypes = [cp, dp, ctypes.c_longlong, ctypes.c_int]
         lib.orc_propagate.restype = ctypes.c_int
+        lib.orc_normalize_m.argtypes = [cp, dp, ctypes.c_double]
+        lib.orc_normalize_m.restype = ctypes.c_int
+        lib.orc_step_m.argtypes = [cp, dp, ctypes.c_double]
+        lib.orc_step_m.restype = ctypes.c_int
         lib.orc_normalize.argtypes = [cp, dp]
         lib.orc_normalize.restype = ctypes.c_int
         lib.orc_norm.argtypes = [cp, dp]
@@ -126,6 +130,21 @@ def propagate(p, psi, nsteps, mode):
 def normalize(p, psi):
     a = _buf(psi, p)
     _check(_load().orc_normalize(ctypes.byref(_params(p)), _ptr(a)), "orc_normalize")
+    return a
+
+
+def normalize_m(p, psi, m):
+    """Magnetisation-constrained normalisation: N = 1 and N+ - N- = m."""
+    a = _buf(psi, p)
+    _check(_load().orc_normalize_m(ctypes.byref(_params(p)), _ptr(a), float(m)), "orc_normalize_m")
+    return a
+
+
+def propagate_m(p, psi, nsteps, m):
+    """Imaginary-time steps with the magnetisation-constrained normalisation (gamma = R = 0)."""
+    a = _buf(psi, p)
+    for _ in range(int(nsteps)):
+        _check(_load().orc_step_m(ctypes.byref(_params(p)), _ptr(a), float(m)), "orc_step_m")
     return a
 
 

@@ -281,3 +281,47 @@ def test_oracle_rejects_bad_parameters():
     p = tiny(dt=-1.0)
     with pytest.raises(oracle.OracleError):
         oracle.step(p, inputs.random_state(7, 6), IMAG)
+
+
+# ---------------------------------------------------------------------------
+# Magnetisation-constrained normalisation (both conditions below Eq. S.5).
+def _norms(p, psi):
+    _, _, dx, dy = dense.axes(p)
+    return np.sum(np.abs(psi) ** 2, axis=(1, 2)) * dx * dy
+
+
+@pytest.mark.parametrize("m", [-0.4, 0.0, 0.3])
+def test_constrained_normalisation_meets_both_conditions(m):
+    p = tiny(so_type=0, rabi=0.0)
+    psi = inputs.random_state(p["nx"], p["ny"], seed=71)
+    before = _norms(p, psi)
+    out = oracle.normalize_m(p, psi, m)
+    after = _norms(p, out)
+    assert abs(after.sum() - 1) < 1e-14 and abs(after[0] - after[2] - m) < 1e-14
+    sig = np.sqrt(after / before)
+    assert abs(sig[0] * sig[2] - sig[1] ** 2) < 1e-14  # the flow's extra condition
+
+
+def test_constrained_normalisation_maps_the_rotated_ferromagnetic_populations():
+    # populations (1/4, 1/2, 1/4) -> ((1+m)^2/4, (1-m^2)/2, (1-m)^2/4): the spin-rotated
+    # fully polarised family, closed under the projection
+    p = dict(nx=8, ny=8, xlen=4.0, ylen=4.0, dt=0.01)
+    g = inputs.gaussian_state(8, 8, 4.0, 4.0, frac=(0.25, 0.5, 0.25), seed=3, phase_noise=0.0)
+    for m in (-0.5, 0.2, 0.7):
+        n = _norms(p, oracle.normalize_m(p, g, m))
+        assert np.allclose(n, [(1 + m) ** 2 / 4, (1 - m * m) / 2, (1 - m) ** 2 / 4], atol=1e-14)
+
+
+def test_constrained_imaginary_time_keeps_m_and_lowers_energy():
+    p = dict(nx=24, ny=24, xlen=12.0, ylen=12.0, dt=0.01, c0=40.0, c2=-3.0, omeg=0.3)
+    psi = inputs.gaussian_state(24, 24, 12.0, 12.0, frac=(0.5, 0.3, 0.2), seed=8)
+    es = []
+    for _ in range(40):
+        psi = oracle.propagate_m(p, psi, 1, 0.25)
+        o = oracle.observables(p, psi)
+        assert abs(o["norm_total"] - 1) < 1e-13 and abs(o["magnetization"] - 0.25) < 1e-13
+        es.append(o["energy"])
+    assert np.all(np.diff(es[1:]) <= 1e-12 * abs(es[0]))
+    # SO or Rabi coupling does not conserve m: the constrained flow is rejected there
+    with pytest.raises(oracle.OracleError):
+        oracle.propagate_m(dict(p, rabi=0.1), psi, 1, 0.25)
