@@ -129,6 +129,13 @@ int gp_propagate(gp_handle* h, long long nsteps, int mode);
  * propagates in FP64 from then on.  On a GP_FP64 handle it equals gp_propagate. */
 int gp_refine_fp64(gp_handle* h, long long nsteps, int mode);
 
+/* Magnetisation-constrained imaginary time (both conditions printed below Eq.
+ * S.5): with enable != 0, every imaginary-time step ends with psi_c <- sigma_c psi_c
+ * such that N = 1 and N_{+1} - N_{-1} = m, with sigma_{+1} sigma_{-1} = sigma_0^2
+ * (the normalised gradient flow for spin-1 condensates).  Only for gamma = R = 0,
+ * where m is conserved by the equations (GP_ERR_ARG otherwise); |m| < 1. */
+int gp_set_magnetization(gp_handle* h, int enable, double m);
+
 /* Computes the observables of the current state on the device (FP64, fixed
  * reduction order, so repeated calls give bitwise identical results).
  * Returns GP_ERR_NONFINITE (and still fills *out) if psi holds NaN or Inf. */
@@ -204,6 +211,16 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued);
  * (complex128, may be NULL) receives the result once it is done; release != 0
  * forgets a finished solve. */
 int gp_batch_poll(gp_batch* b, long long id, int* state, long long* steps, gp_obs* obs, double* psi_out, int release);
+
+/* Autotuner: for the handle's current precision and the given mode, times the
+ * x-pass and the y-pass for each candidate tiling -- lines per CTA (1, 2, 4),
+ * one CTA or a 2-CTA cluster per line group, chunk lengths of the parallel
+ * Thomas solve -- on the handle's stream, and keeps the fastest for later
+ * propagation.  The state is saved and restored, so tuning does not change the
+ * solve; results stay within the parity tolerances (only the summation order of
+ * partial norms and the chunking change).  *ms_out (may be NULL) receives the
+ * tuned x-pass + y-pass time.  Allocates one temporary copy of psi. */
+int gp_autotune(gp_handle* h, int mode, double* ms_out);
 
 /* Human-readable text for a gp_status. */
 const char* gp_strerror(int status);

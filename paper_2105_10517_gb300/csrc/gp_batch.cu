@@ -112,6 +112,12 @@ namespace {
 
 int policy_precision(int policy) { return policy == GP_POLICY_FP32_REFINE ? GP_FP32_MIXED : GP_FP64; }
 
+LineTiling with_bulk(LineTiling t, int bulk)
+{
+    t.bulk = bulk;
+    return t;
+}
+
 // Puts one running instance into its precision group's launch lists.
 template <typename C>
 void add_instance(Group<C>& g, gp_handle* h, const PassArgsT<C>& ax, PassArgsT<C> ay)
@@ -284,10 +290,17 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
         Request& q = kv.second;
         if (q.state != GP_REQ_RUNNING) continue;
         const CoefSet& cs = q.h->coef[GP_IMAG];
+        // batched launches use the unsplit tilings (no clusters in the work list)
         if (q.h->active == GP_FP32_MIXED) {
-            add_instance(b->g32, q.h, pass_args_f32(q.h, cs, 0), pass_args_f32(q.h, cs, 1));
+            PassArgsF ax = pass_args_f32(q.h, cs, 0), ay = pass_args_f32(q.h, cs, 1);
+            ax.t = with_bulk(cs.fux, ax.t.bulk);
+            ay.t = with_bulk(cs.fuy, ay.t.bulk);
+            add_instance(b->g32, q.h, ax, ay);
         } else {
-            add_instance(b->g64, q.h, pass_args(q.h, cs, 0), pass_args(q.h, cs, 1));
+            PassArgs ax = pass_args(q.h, cs, 0), ay = pass_args(q.h, cs, 1);
+            ax.t = with_bulk(cs.ux, ax.t.bulk);
+            ay.t = with_bulk(cs.uy, ay.t.bulk);
+            add_instance(b->g64, q.h, ax, ay);
         }
         run.push_back(&q);
     }

@@ -75,44 +75,66 @@ double max_cp(const gp_params& p, int dir, int mode)
 // with H the rows until the factorisation has converged (contraction |c'|^2
 // per row); R lines per CTA within ~100 KB of shared memory (two CTAs per SM)
 // and 512 threads.
-int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32)
+int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_req, LineTiling* t)
 {
     if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
+    if (S < 1 || S > 2 || R < 1) return GP_ERR_ARG;
     const double bits = fp32 ? 26.0 : 60.0;
     const size_t elem = fp32 ? sizeof(float2) : sizeof(double2);
     int F = cpmax > 0 ? (int)std::ceil(bits * std::log(2.0) / -std::log(cpmax)) + 1 : 1;
     int H = (F + 1) / 2 + 2;
     if (F > kFix || H > kHead) return GP_ERR_UNSUPPORTED;
-    int m = std::max(16, H + F);
+    int m = std::max(std::max(16, H + F), m_req);
     m = (m + 3) / 4 * 4;
     int Q = (L + m - 1) / m;
-    while (3 * Q > 512) {  // keep one thread per chunk within a CTA
-        m += 4;
-        Q = (L + m - 1) / m;
-    }
-    int Lp = Q * (m + 1) + 1;
+    if (S > 1 && Q < 4) return GP_ERR_ARG;
+    const int Qc = (Q + S - 1) / S;
+    const int Lp = Qc * (m + 1) + 1;
+    if (3 * R * Qc > 512 || R > nlines) return GP_ERR_ARG;
     auto up = [](size_t b) { return (b + 127) / 128 * 128; };
-    auto smem_of = [&](int R) { return up(3 * R * Lp * elem) * 2 + 2 * up(3 * R * Q * elem); };
-    int R = std::max(1, 256 / (3 * Q));
-    if (fp32) R = std::max(R, 4);  // >= 32-byte segments in the transposed store
-    while (R > 1 && (smem_of(R) > 100 * 1024 || 3 * R * Q > 512)) --R;
-    R = std::min(R, nlines);
-    if (smem_of(R) > 227 * 1024) return GP_ERR_UNSUPPORTED;
+    const size_t smem = up(3 * R * Lp * elem) * 2 + 2 * up(3 * R * Qc * elem);
+    if (smem > 227 * 1024) return GP_ERR_UNSUPPORTED;
     t->L = L;
     t->nlines = nlines;
     t->R = R;
     t->m = m;
     t->Q = Q;
+    t->S = S;
+    t->Qc = Qc;
     t->F = std::min(F, m - 1);
     t->Lp = Lp;
-    int thr = std::max(64, 3 * R * Q);
-    t->threads = std::min(512, (thr + 31) / 32 * 32);
-    t->smem = smem_of(R);
+    t->threads = std::min(512, (std::max(32, 3 * R * Qc) + 31) / 32 * 32);
+    t->smem = smem;
     t->off_b = up(3 * R * Lp * elem);
     t->off_cf = 2 * t->off_b;
-    t->off_cb = t->off_cf + up(3 * R * Q * elem);
+    t->off_cb = t->off_cf + up(3 * R * Qc * elem);
     t->bulk = 0;  // set per pass by the caller (needs 16-byte aligned rows)
     return GP_OK;
+}
+
+// Default tiling: the minimum chunk length, lines per CTA within ~100 KB of
+// shared memory and 256 threads, and long lines (>= 256 points) split over a
+// 2-CTA cluster (twice the work units for the SMs, half the shared memory per CTA).
+int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32, int split)
+{
+    LineTiling base;
+    int st = make_tiling(L, nlines, cpmax, fp32, 1, 1, 0, &base);
+    if (st) return st;
+    int m = base.m, Q = base.Q;
+    while (3 * Q > 512) {  // keep one thread per chunk within a CTA
+        m += 4;
+        Q = (L + m - 1) / m;
+    }
+    const int S = (split && L >= 256 && Q >= 8) ? 2 : 1;
+    const int Qc = (Q + S - 1) / S;
+    int R = std::max(1, 256 / (3 * Qc));
+    if (fp32 && S == 1) R = std::max(R, 4);  // >= 32-byte segments in the transposed store
+    if (S > 1) R = 1;
+    R = std::min(R, nlines);
+    for (; R >= 1; --R) {
+        if (make_tiling(L, nlines, cpmax, fp32, S, R, m, t) == GP_OK && (R == 1 || t->smem <= 100 * 1024)) return GP_OK;
+    }
+    return GP_ERR_UNSUPPORTED;
 }
 
 #define CK(x)                                                  \
@@ -161,14 +183,18 @@ int ensure_coef(gp_handle* h, int mode)
     if (cs.valid && same_physics(cs.key, h->p)) return GP_OK;
     const gp_params& p = h->p;
     const bool f32 = wants_fp32(h);
-    LineTiling tx, ty, ftx{}, fty{};
+    LineTiling tx, ty, ftx{}, fty{}, ux, uy, fux{}, fuy{};
     const double cx = max_cp(p, 0, mode), cy = max_cp(p, 1, mode);
     int st = choose_tiling(p.nx, p.ny, cx, &tx);
     if (st) return st;
     if ((st = choose_tiling(p.ny, p.nx, cy, &ty))) return st;
+    if ((st = choose_tiling(p.nx, p.ny, cx, &ux, 0, 0))) return st;
+    if ((st = choose_tiling(p.ny, p.nx, cy, &uy, 0, 0))) return st;
     if (f32) {
         if ((st = choose_tiling(p.nx, p.ny, cx, &ftx, 1))) return st;
         if ((st = choose_tiling(p.ny, p.nx, cy, &fty, 1))) return st;
+        if ((st = choose_tiling(p.nx, p.ny, cx, &fux, 1, 0))) return st;
+        if ((st = choose_tiling(p.ny, p.nx, cy, &fuy, 1, 0))) return st;
     }
     if (!cs.cx) {
         bool ok = cudaMalloc(&cs.cx, sizeof(LineCoef) * 3 * (size_t)p.ny) == cudaSuccess &&
@@ -208,6 +234,10 @@ int ensure_coef(gp_handle* h, int mode)
     cs.ty = ty;
     cs.ftx = ftx;
     cs.fty = fty;
+    cs.ux = ux;
+    cs.uy = uy;
+    cs.fux = fux;
+    cs.fuy = fuy;
     cs.key = p;
     cs.valid = true;
     return GP_OK;
@@ -226,6 +256,12 @@ void fill_common(gp_handle* h, PassArgsT<C>& a)
     a.do_p = 1;
     a.do_solve = 1;
     a.err = h->flag;
+    a.dx = h->p.xlen / h->p.nx;
+    a.dy = h->p.ylen / h->p.ny;
+    a.x0 = -0.5 * h->p.xlen + 0.5 * a.dx;
+    a.y0 = -0.5 * h->p.ylen + 0.5 * a.dy;
+    a.wx = h->p.wx;
+    a.wy = h->p.wy;
 }
 
 // Rows can be staged with cp.async.bulk when every row starts on a 16-byte
@@ -325,7 +361,7 @@ int sync_status(gp_handle* h)
     return GP_OK;
 }
 
-int y_blocks(const LineTiling& t) { return (t.nlines + t.R - 1) / t.R; }
+int y_blocks(const LineTiling& t) { return (t.nlines + t.R - 1) / t.R * t.S; }
 
 size_t handle_bytes(const gp_params& p)
 {
@@ -339,13 +375,25 @@ size_t handle_bytes(const gp_params& p)
 
 // Launch sequence of n steps (x-pass, y-pass and, in imaginary time, the
 // normalisation) on the handle's stream.
+template <typename C>
+int apply_sigma(gp_handle* h, const PassArgsT<C>& ay)
+{
+    return launch_apply_comp_scale(ay.out, (size_t)h->p.nx * h->p.ny, h->scal + 3, h->stream);
+}
+
 template <typename A>
 int enqueue_steps(gp_handle* h, int mode, const A& ax, const A& ay, int gy, long long n)
 {
     for (long long s = 0; s < n; ++s) {
         LK(launch_xpass(ax, mode, h->stream));
         LK(launch_ypass(ay, mode, h->stream));
-        if (mode == GP_IMAG) LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
+        if (mode == GP_IMAG && h->mcon) {
+            // magnetisation-constrained normalisation, applied at once
+            LK(launch_finalize_m(h->partials, gy, cell(h), h->m_target, h->scal + 3, h->flag, h->stream));
+            LK(apply_sigma(h, ay));
+        } else if (mode == GP_IMAG) {
+            LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
+        }
     }
     return GP_OK;
 }
@@ -394,18 +442,25 @@ int propagate_active(gp_handle* h, long long nsteps, int mode)
     if (mode == GP_REAL && (st = flush_scale(h))) return st;
     const bool f32 = h->active == GP_FP32_MIXED;
     const int gy = y_blocks(f32 ? cs.fty : cs.ty);
-    if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
+    const bool mc = mode == GP_IMAG && h->mcon;
+    if (gy * (mc ? 3 : 1) > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
+    if (mc) {
+        if (gamma_of(h->p) != 0.0 || h->p.rabi != 0.0) return GP_ERR_ARG;  // m is not conserved there
+        if ((st = flush_scale(h))) return st;
+    }
     if (f32) {
         PassArgsF ax = pass_args_f32(h, cs, 0), ay = pass_args_f32(h, cs, 1);
         if (mode == GP_IMAG) ay.partials = h->partials;
+        ay.mcomp = mc;
         st = run_steps(h, mode, ax, ay, gy, nsteps);
     } else {
         PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
         if (mode == GP_IMAG) ay.partials = h->partials;
+        ay.mcomp = mc;
         st = run_steps(h, mode, ax, ay, gy, nsteps);
     }
     if (st) return st;
-    if (mode == GP_IMAG) h->scale_pending = true;
+    if (mode == GP_IMAG && !mc) h->scale_pending = true;
     h->steps += nsteps;
     return GP_OK;
 }
@@ -455,7 +510,7 @@ int gp_create(const gp_params* params, void* cuda_stream, gp_handle** out)
               cudaMalloc(&h->partials, kNormBlocksMax * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&h->obs_part, (size_t)obs_blocks(h->p.nx, h->p.ny) * obs_slots() * sizeof(double)) ==
                   cudaSuccess &&
-              cudaMalloc(&h->scal, 3 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&h->scal, 6 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&h->obs_out, 8 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&h->flag, sizeof(int)) == cudaSuccess;
     if (ok && wants_fp32(h))
@@ -507,6 +562,16 @@ int gp_set_params(gp_handle* h, const gp_params* params)
         return GP_ERR_ARG;
     h->p = *params;
     drop_graphs(h);  // the captured launches hold c0, c2, R and dt by value
+    return GP_OK;
+}
+
+int gp_set_magnetization(gp_handle* h, int enable, double m)
+{
+    if (!h || !(std::isfinite(m)) || !(m > -1.0 && m < 1.0)) return GP_ERR_ARG;
+    if (enable && (gamma_of(h->p) != 0.0 || h->p.rabi != 0.0)) return GP_ERR_ARG;
+    h->mcon = enable ? 1 : 0;
+    h->m_target = m;
+    drop_graphs(h);  // the captured step sequence depends on the normalisation
     return GP_OK;
 }
 
@@ -643,6 +708,92 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out)
     CK(cudaEventElapsedTime(&ms_out[3], h->ev[0], h->ev[3]));
     h->steps += 1;
     return GP_OK;
+}
+
+extern "C++" {
+// Times one pass (x: dir 0, y: dir 1) with the given tiling: best of three
+// launches on the handle's stream, in ms (negative if the launch fails).
+template <typename A>
+float time_pass(gp_handle* h, A a, int dir, int mode)
+{
+    a.partials = nullptr;
+    float best = -1.0f;
+    for (int rep = 0; rep < 4; ++rep) {
+        if (cudaEventRecord(h->ev[0], h->stream) != cudaSuccess) return -1.0f;
+        int rc = dir == 0 ? launch_xpass(a, mode, h->stream) : launch_ypass(a, mode, h->stream);
+        if (rc || cudaEventRecord(h->ev[1], h->stream) != cudaSuccess || cudaEventSynchronize(h->ev[1]) != cudaSuccess)
+            return -1.0f;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+        if (rep > 0 && (best < 0 || ms < best)) best = ms;  // the first launch warms up
+    }
+    return best;
+}
+
+}  // extern "C++"
+
+int gp_autotune(gp_handle* h, int mode, double* ms_out)
+{
+    if (!h || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
+    int st = ensure_coef(h, mode);
+    if (st) return st;
+    for (auto& e : h->ev)
+        if (!e) CK(cudaEventCreate(&e));
+    CoefSet& cs = h->coef[mode];
+    const gp_params& p = h->p;
+    const bool f32 = h->active == GP_FP32_MIXED;
+    const size_t bytes = n_elems(h) * (f32 ? sizeof(float2) : sizeof(double2));
+    // the y-pass overwrites psi: keep a copy and restore it afterwards
+    void* keep = nullptr;
+    if (cudaMalloc(&keep, bytes) != cudaSuccess) return GP_ERR_OOM;
+    void* state = f32 ? (void*)h->psi32 : (void*)h->psi;
+    if (cudaMemcpyAsync(keep, state, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) {
+        cudaFree(keep);
+        return GP_ERR_CUDA;
+    }
+    double best_total = 0;
+    for (int dir = 0; dir < 2 && st == GP_OK; ++dir) {
+        const int L = dir == 0 ? p.nx : p.ny, nl = dir == 0 ? p.ny : p.nx;
+        const double cp = max_cp(p, dir, mode);
+        LineTiling& cur = f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty);
+        LineTiling best = cur;
+        float best_ms = -1.0f;
+        const int ms_add[] = {0, 4, 8, 16, 32};
+        for (int S = 1; S <= 2; ++S)
+            for (int R : {1, 2, 4})
+                for (int add : ms_add) {
+                    LineTiling t;
+                    if (make_tiling(L, nl, cp, f32, S, R, cur.m - (cur.m % 4) + add, &t) != GP_OK) continue;
+                    if (S > 1 && L < 64) continue;
+                    float ms;
+                    if (f32) {
+                        PassArgsF a = pass_args_f32(h, cs, dir);
+                        t.bulk = a.t.bulk;
+                        a.t = t;
+                        ms = time_pass(h, a, dir, mode);
+                    } else {
+                        PassArgs a = pass_args(h, cs, dir);
+                        t.bulk = a.t.bulk;
+                        a.t = t;
+                        ms = time_pass(h, a, dir, mode);
+                    }
+                    if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
+                        best_ms = ms;
+                        best = t;
+                    }
+                }
+        if (best_ms < 0) st = GP_ERR_CUDA;
+        cur = best;
+        cur.bulk = 0;
+        best_total += best_ms;
+    }
+    cudaGetLastError();
+    if (cudaMemcpyAsync(state, keep, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) st = GP_ERR_CUDA;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(keep);
+    drop_graphs(h);
+    if (ms_out) *ms_out = best_total;
+    return st;
 }
 
 int gp_apply_substep(gp_handle* h, int which, int mode)

@@ -5,7 +5,7 @@
 
 namespace gpspin {
 
-constexpr int kNormBlocksMax = 4096;
+constexpr int kNormBlocksMax = 16384;
 
 // Coefficient tables and tilings of one mode (imaginary or real time).
 struct CoefSet {
@@ -19,7 +19,8 @@ struct CoefSet {
     LineCoefF* fy = nullptr;
     float2* fex = nullptr;
     float2* fey = nullptr;
-    LineTiling tx{}, ty{}, ftx{}, fty{};
+    LineTiling tx{}, ty{}, ftx{}, fty{};  // single-instance launches (may span 2-CTA clusters)
+    LineTiling ux{}, uy{}, fux{}, fuy{};  // unsplit, for batched launches
 };
 
 }  // namespace gpspin
@@ -36,7 +37,8 @@ struct gp_handle {
     float2* work32 = nullptr;
     double* partials = nullptr;
     double* obs_part = nullptr;
-    double* scal = nullptr;    // [0] pending normalisation, [1] last norm, [2] the constant 1
+    double* scal = nullptr;    // [0] pending normalisation, [1] last norm, [2] the constant 1,
+                               // [3..5] per-component factors of the constrained normalisation
     double* obs_out = nullptr; // [8]
     int* flag = nullptr;       // bit0 coefficient convergence, bit1 norm, bit2 observables, bit3 copy timeout
     gpspin::CoefSet coef[2];   // per mode
@@ -44,6 +46,8 @@ struct gp_handle {
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [precision][mode]
     bool scale_pending = false;
     long long steps = 0;
+    int mcon = 0;              // imaginary time keeps N = 1 and N+ - N- = m_target
+    double m_target = 0.0;
 };
 
 namespace gpspin {

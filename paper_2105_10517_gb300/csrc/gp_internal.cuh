@@ -61,7 +61,9 @@ struct LineTiling {
     int m;      // chunk length of the parallel Thomas solve
     int Q;      // chunks per line = ceil(L / m)
     int F;      // fixup length (|c'_inf|^F below the precision's rounding), F < m
-    int Lp;     // padded smem stride of one line-channel: Q (m + 1) + 1
+    int Lp;     // padded smem stride of one line-channel in a CTA: Qc (m + 1) + 1
+    int S;      // CTAs per line group (a thread-block cluster when S > 1)
+    int Qc;     // chunks per CTA = ceil(Q / S); CTA rank r holds chunks r*Qc ..
     int threads;
     size_t smem;
     size_t off_b;  // byte offsets in dynamic smem of the second line array (also the
@@ -80,12 +82,15 @@ struct PassArgsT {
     int do_p;                  // x-pass: apply the pointwise substep
     int do_solve;              // apply the CN solve (0: channels pass through)
     const double* scale;       // device scalar: pending normalisation (x-pass)
-    double* partials;          // y-pass: per-CTA sum |psi|^2
+    double* partials;          // y-pass: per-CTA sum |psi|^2 (per component when mcomp)
+    int mcomp;                 // y-pass: three partials per CTA, one per component
     int* err;                  // status bits set by the kernel (8: bulk-copy wait timed out)
     // pointwise substep constants (x-pass)
     const C* ex;               // [nx] exp(-tau' wx^2 x^2 / 2)
     const C* ey;               // [ny] exp(-tau' wy^2 y^2 / 2)
     double dt, c0, c2, rabi;
+    // grid and trap (the complex64 pass evaluates the trap factor inline)
+    double x0, dx, y0, dy, wx, wy;
 };
 using PassArgs = PassArgsT<double2>;
 using PassArgsF = PassArgsT<float2>;
@@ -97,7 +102,11 @@ int eta_of(const gp_params& p);
 double gamma_of(const gp_params& p);
 double max_cp(const gp_params& p, int dir, int mode);
 // fp32 = 1: tiling for complex64 lines (fixups to 2^-26 instead of 2^-60)
-int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32 = 0);
+// split = 1 allows a line group to span a 2-CTA cluster (not for batched launches).
+int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32 = 0, int split = 1);
+// A specific tiling (autotuner candidates): S CTAs per line group, R lines per
+// CTA, chunk length m (raised to the minimum the precision needs).
+int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m, LineTiling* t);
 
 // launchers (gp_sweeps.cu)
 int launch_coef(LineCoef* coef, int nlines, int dir, int mode, double h, double line_len, double line_h,
@@ -130,6 +139,9 @@ struct FinArgs {
     double* scale;
 };
 int launch_finalize_norm_batched(const FinArgs* fin, const int* n_inst, int capacity, int* flag, cudaStream_t st);
+int launch_finalize_m(const double* partials, int n, double da, double m, double* sigma, int* flag, cudaStream_t st);
+int launch_apply_comp_scale(double2* psi, size_t plane, const double* sigma, cudaStream_t st);
+int launch_apply_comp_scale(float2* psi, size_t plane, const double* sigma, cudaStream_t st);
 int launch_apply_scale(double2* psi, size_t n, double* scale, cudaStream_t st);
 int launch_apply_scale(float2* psi, size_t n, double* scale, cudaStream_t st);
 int launch_set_scalar(double* p, double v, cudaStream_t st);

@@ -103,9 +103,12 @@ extern "C" int gp_propagate_noalloc(const gp_params* params, double* psi_dev, lo
     const Scratch& S = g_scratch[dev];
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
+    // unsplit tilings: one CTA per line group, so the y-pass writes at most
+    // kMaxLine partial norms into g_partials
     LineTiling tx, ty;
-    if ((st = choose_tiling(p.nx, p.ny, max_cp(p, 0, mode), &tx))) return st;
-    if ((st = choose_tiling(p.ny, p.nx, max_cp(p, 1, mode), &ty))) return st;
+    if ((st = choose_tiling(p.nx, p.ny, max_cp(p, 0, mode), &tx, 0, 0))) return st;
+    if ((st = choose_tiling(p.ny, p.nx, max_cp(p, 1, mode), &ty, 0, 0))) return st;
+    if ((ty.nlines + ty.R - 1) / ty.R * ty.S > kMaxLine) return GP_ERR_TOO_LARGE;
 
     // The arrays keep the previous call's contents: the flag must start at zero
     // and the scale at one; every other array is fully rewritten below.
@@ -142,10 +145,16 @@ extern "C" int gp_propagate_noalloc(const gp_params* params, double* psi_dev, lo
     ay.coef = S.cy;
     ay.t = ty;
     ax.err = ay.err = S.flag;
+    ax.dx = ay.dx = dx;
+    ax.dy = ay.dy = dy;
+    ax.x0 = ay.x0 = -0.5 * p.xlen + 0.5 * dx;
+    ax.y0 = ay.y0 = -0.5 * p.ylen + 0.5 * dy;
+    ax.wx = ay.wx = p.wx;
+    ax.wy = ay.wy = p.wy;
     ax.t.bulk = ((size_t)p.nx * sizeof(double2)) % 16 == 0 && (reinterpret_cast<uintptr_t>(psi_dev) % 16) == 0;
     ay.t.bulk = ((size_t)p.ny * sizeof(double2)) % 16 == 0;
     const double da = dx * dy;
-    const int gy = (ty.nlines + ty.R - 1) / ty.R;
+    const int gy = (ty.nlines + ty.R - 1) / ty.R * ty.S;
     if (mode == GP_IMAG) ay.partials = S.partials;
     for (long long s = 0; s < nsteps; ++s) {
         NL(launch_xpass(ax, mode, stream));

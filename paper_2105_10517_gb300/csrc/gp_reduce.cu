@@ -103,6 +103,50 @@ __global__ void narrow_kernel(float2* dst, const double2* src, size_t n)
 
 __global__ void set_scalar_kernel(double* p, double v) { *p = v; }
 
+// Magnetisation-constrained normalisation: N_c = dA * sum of the per-component
+// partials (index order); sigma_c makes N = 1 and N+ - N- = m with
+// sigma+ sigma- = sigma0^2:  sigma0^2 = (1 - m^2) / (N0 + sqrt(N0^2 m^2 + 4 (1 - m^2) N+ N-)),
+// sigma+-^2 = (1 +- m - sigma0^2 N0) / (2 N+-); an empty +-1 component keeps 1.
+__global__ void __launch_bounds__(kRedThreads) finalize_m_kernel(const double* partials, int n, double da, double m,
+                                                                 double* sigma, int* flag)
+{
+    __shared__ double sh[32];
+    __shared__ double nc[3];
+    for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+        for (int k = threadIdx.x; k < n; k += kRedThreads) acc += partials[3 * k + c];
+        double t = block_sum(acc, sh);
+        if (threadIdx.x == 0) nc[c] = t * da;
+    }
+    if (threadIdx.x == 0) {
+        const double np_ = nc[0], n0 = nc[1], nm = nc[2];
+        const double a = (1.0 - m * m) / (n0 + sqrt(n0 * n0 * m * m + 4.0 * (1.0 - m * m) * np_ * nm));
+        double s0 = sqrt(a);
+        double sp = np_ > 0 ? sqrt((1.0 + m - a * n0) / (2.0 * np_)) : 1.0;
+        double sm = nm > 0 ? sqrt((1.0 - m - a * n0) / (2.0 * nm)) : 1.0;
+        if (!(isfinite(s0) && isfinite(sp) && isfinite(sm))) {
+            s0 = sp = sm = 1.0;
+            atomicOr(flag, 2);
+        }
+        sigma[0] = sp;
+        sigma[1] = s0;
+        sigma[2] = sm;
+    }
+}
+
+template <typename C>
+__global__ void apply_comp_scale_kernel(C* psi, size_t plane, const double* sigma)
+{
+    const double s[3] = {sigma[0], sigma[1], sigma[2]};
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 3 * plane; k += (size_t)gridDim.x * blockDim.x) {
+        const double f = s[k / plane];
+        C v = psi[k];
+        v.x = f * v.x;
+        v.y = f * v.y;
+        psi[k] = v;
+    }
+}
+
 // Batched normalisation: CTA b finalises instance b (same arithmetic and order
 // as finalize_norm_kernel, so an instance gets the same scale alone or batched).
 __global__ void __launch_bounds__(kRedThreads) finalize_norm_batched_kernel(const FinArgs* fin, const int* n_inst,
@@ -311,6 +355,24 @@ int launch_finalize_norm_batched(const FinArgs* fin, const int* n_inst, int capa
 {
     if (capacity <= 0) return 0;
     finalize_norm_batched_kernel<<<capacity, kRedThreads, 0, st>>>(fin, n_inst, flag);
+    return report_cuda(cudaGetLastError(), __func__);
+}
+
+int launch_finalize_m(const double* partials, int n, double da, double m, double* sigma, int* flag, cudaStream_t st)
+{
+    finalize_m_kernel<<<1, kRedThreads, 0, st>>>(partials, n, da, m, sigma, flag);
+    return report_cuda(cudaGetLastError(), __func__);
+}
+
+int launch_apply_comp_scale(double2* psi, size_t plane, const double* sigma, cudaStream_t st)
+{
+    apply_comp_scale_kernel<<<grid_for(3 * plane, 256, 1216), 256, 0, st>>>(psi, plane, sigma);
+    return report_cuda(cudaGetLastError(), __func__);
+}
+
+int launch_apply_comp_scale(float2* psi, size_t plane, const double* sigma, cudaStream_t st)
+{
+    apply_comp_scale_kernel<<<grid_for(3 * plane, 256, 1216), 256, 0, st>>>(psi, plane, sigma);
     return report_cuda(cudaGetLastError(), __func__);
 }
 

@@ -11,6 +11,9 @@
 // many threads run at once (the chunked Thomas solve below).
 #include "gp_internal.cuh"
 #include <cmath>
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 namespace gpspin {
 
@@ -106,22 +109,53 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err)
     return true;
 }
 
-// Stages rows row(r, c) = base + (c * plane + (line0 + r) * L) of length L for
-// r < nl, c < 3 into dst[(r * 3 + c) * L].  Rows must be 16-byte aligned.
+// Stages row segments base + c * plane + (line0 + r) * L + k0 .. + len for
+// r < nl, c < 3 into dst[(r * 3 + c) * len].  Segments must be 16-byte aligned
+// and a multiple of 16 bytes long.
 template <typename C>
-__device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, int line0, int nl, int L,
-                                           uint64_t* mbar, int* err)
+__device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, int line0, int nl, int L, int k0,
+                                           int len, uint64_t* mbar, int* err)
 {
     if (threadIdx.x == 0) mbar_init(mbar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t row_bytes = (uint32_t)(L * sizeof(C));
-        mbar_expect_tx(mbar, row_bytes * 3u * (uint32_t)nl);
+        const uint32_t seg_bytes = (uint32_t)(len * sizeof(C));
+        mbar_expect_tx(mbar, seg_bytes * 3u * (uint32_t)nl);
         for (int r = 0; r < nl; ++r)
             for (int c = 0; c < 3; ++c)
-                bulk_g2s(dst + (size_t)(r * 3 + c) * L, base + c * plane + (size_t)(line0 + r) * L, row_bytes, mbar);
+                bulk_g2s(dst + (size_t)(r * 3 + c) * len, base + c * plane + (size_t)(line0 + r) * L + k0, seg_bytes,
+                         mbar);
     }
     return mbar_wait_bounded(mbar, err);
+}
+
+// The part of a line group one CTA works on: lines line0 .. line0 + nl - 1,
+// chunks q0 .. q0 + nq - 1, positions k0 .. k0 + len - 1.  With S > 1 the S CTAs
+// of a cluster share the line group (cluster rank = part index).
+struct Part {
+    int rank, line0, nl, q0, nq, k0, len;
+};
+
+__device__ __forceinline__ Part make_part(const LineTiling& T, int cta)
+{
+    Part P;
+    P.rank = T.S > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    P.line0 = (cta / T.S) * T.R;
+    P.nl = min(T.R, T.nlines - P.line0);
+    P.q0 = P.rank * T.Qc;
+    P.nq = max(0, min(T.Qc, T.Q - P.q0));
+    P.k0 = P.q0 * T.m;
+    P.len = max(0, min(T.L, P.k0 + T.Qc * T.m) - P.k0);
+    return P;
+}
+
+// Barrier over the CTAs that share a line group.
+__device__ __forceinline__ void group_sync(const LineTiling& T)
+{
+    if (T.S > 1)
+        cg::this_cluster().sync();
+    else
+        __syncthreads();
 }
 
 // ------------------------------------------------------------------ K1 ----
@@ -211,6 +245,7 @@ struct PConstT {
     R dtc2;  // dt c2 s^2
     R dtr;   // dt R / sqrt(2)
     R s;     // pending normalisation
+    R dt;
 };
 
 // v = M psi for M = dt B.Sigma, with bx = dt B_x/sqrt2, by = dt B_y/sqrt2, bz = dt B_z.
@@ -310,8 +345,11 @@ __device__ __forceinline__ void scalar_cis(double x, double& cs, double& sn)
 }
 __device__ __forceinline__ void scalar_cis(float x, float& cs, float& sn) { sincosf(x, &sn, &cs); }
 
+// ev: trap factor from the tables (complex128 pass); tv: dt V added to the
+// scalar exponent instead (complex64 pass, ev = 1, one expf/sincosf per site).
 template <int MODE, typename C>
-__device__ __forceinline__ void pointwise(C& a, C& b, C& c, C ev, const PConstT<typename RealOf<C>::type>& k)
+__device__ __forceinline__ void pointwise(C& a, C& b, C& c, C ev, typename RealOf<C>::type tv,
+                                          const PConstT<typename RealOf<C>::type>& k)
 {
     typedef typename RealOf<C>::type R;
     R rp = fma(a.x, a.x, a.y * a.y);
@@ -330,7 +368,7 @@ __device__ __forceinline__ void pointwise(C& a, C& b, C& c, C ev, const PConstT<
     C va, vb, vc, wa, wb, wc;
     spin_mv(bx, by, bz, a, b, c, va, vb, vc);
     spin_mv(bx, by, bz, va, vb, vc, wa, wb, wc);
-    const R x = k.dtc0 * rho;
+    const R x = fma(k.dtc0, rho, tv);
     if (MODE == 1) {
         // t = psi - i s1 v - s2 w
         C ta = mkc<C>(fma(s1, va.y, fma(-s2, wa.x, a.x)), fma(-s1, va.x, fma(-s2, wa.y, a.y)));
@@ -408,20 +446,29 @@ __device__ __forceinline__ void from_sigma_x(C xp, C x0, C xm, C& a, C& b, C& c)
 // keeps chunk-parallel accesses on distinct banks).
 template <typename C>
 __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const LineCoefT<C>* coef,
-                                               const LineTiling& T, int nl)
+                                               const LineTiling& T, const Part& P)
 {
     typedef typename RealOf<C>::type R;
-    const int m = T.m, Q = T.Q, F = T.F, L = T.L, Lp = T.Lp;
-    const int nthr = 3 * nl * Q;
+    const int m = T.m, Q = T.Q, F = T.F, L = T.L, Lp = T.Lp, Qc = T.Qc;
+    const int nthr = 3 * P.nl * Qc;
     const int tid = threadIdx.x;
-    const bool active = tid < nthr;
-    const int q = active ? tid % Q : 0;
-    const int lc = active ? tid / Q : 0;  // r * 3 + ch
+    const int ql = tid % Qc;               // chunk within the CTA
+    const int lc = min(tid / Qc, 3 * max(P.nl, 1) - 1);  // r * 3 + ch
+    const bool active = tid < nthr && ql < P.nq;
+    const int q = P.q0 + ql;               // chunk within the line
     const int start = q * m;
-    const int len = min(m, L - start);
-    const LineCoefT<C>* Co = coef + lc;   // coef already offset to the CTA's first line
-    C* __restrict__ pa = sa + lc * Lp + q * (m + 1);
-    C* __restrict__ pbf = sb + lc * Lp + q * (m + 1);
+    const int len = max(0, min(m, L - start));
+    const LineCoefT<C>* Co = coef + lc;    // coef already offset to the CTA's first line
+    C* __restrict__ pa = sa + lc * Lp + ql * (m + 1);
+    C* __restrict__ pbf = sb + lc * Lp + ql * (m + 1);
+    // carries of the neighbouring CTAs of the cluster (distributed shared memory)
+    const C* cf_prev = cf;
+    const C* cb_next = cb;
+    if (T.S > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        if (P.rank > 0) cf_prev = cl.map_shared_rank(cf, P.rank - 1);
+        if (P.rank < T.S - 1) cb_next = cl.map_shared_rank(cb, P.rank + 1);
+    }
 
     // Converged factorisation (rows >= kHead - 1) in registers; rows inside the
     // table head are fetched with a predicated load (no divergent branch).
@@ -440,14 +487,24 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
             y = cfnma(g, y, cmul(inv, pa[t]));
             pbf[t] = y;
         }
-        cf[lc * Q + q] = y;
+        cf[lc * Qc + ql] = y;
     }
-    __syncthreads();
+    group_sync(T);
     if (active) {
         if (q > 0) {
-            C yc = cf[lc * Q + q - 1];
+            C yc = ql > 0 ? cf[lc * Qc + ql - 1] : cf_prev[lc * Qc + Qc - 1];
             int nf = min(F, len);
-            for (int t = 0; t < nf; ++t) pbf[t] = cfma(Co->pf[t], yc, pbf[t]);
+            if constexpr (sizeof(R) == 4) {
+                // complex64: powers (-g_inf)^(t+1) by a running product (no table loads)
+                const C mg = mkc<C>(-g_c.x, -g_c.y);
+                C pw = mg;
+                for (int t = 0; t < nf; ++t) {
+                    pbf[t] = cfma(pw, yc, pbf[t]);
+                    pw = cmul(pw, mg);
+                }
+            } else {
+                for (int t = 0; t < nf; ++t) pbf[t] = cfma(Co->pf[t], yc, pbf[t]);
+            }
         }
         C w = mkc<C>(R(0), R(0));
 #pragma unroll 4
@@ -458,22 +515,39 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
             w = cfnma(cp, w, pbf[t]);
             pbf[t] = w;
         }
-        cb[lc * Q + q] = w;
+        cb[lc * Qc + ql] = w;
     }
-    __syncthreads();
+    group_sync(T);
     if (active) {
         const bool fix = q < Q - 1;
-        C wc = fix ? cb[lc * Q + q + 1] : mkc<C>(R(0), R(0));
+        C wc = !fix ? mkc<C>(R(0), R(0)) : (ql < P.nq - 1 ? cb[lc * Qc + ql + 1] : cb_next[lc * Qc + 0]);
         const int tf = fix ? len - F : len;  // points t >= tf get the backward fixup
+        if constexpr (sizeof(R) == 4) {
+            // complex64: powers (-c'_inf)^(len - t) by a running product, applied first
+            const C mc = mkc<C>(-cp_c.x, -cp_c.y);
+            C pw = mc;
+            for (int t = len - 1; t >= tf; --t) {
+                pbf[t] = cfma(pw, wc, pbf[t]);
+                pw = cmul(pw, mc);
+            }
 #pragma unroll 4
-        for (int t = 0; t < len; ++t) {
-            C w = pbf[t];
-            if (t >= tf) w = cfma(Co->pb[len - t - 1], wc, w);
-            C ph = pa[t];
-            pa[t] = mkc<C>(fma(R(2), w.x, -ph.x), fma(R(2), w.y, -ph.y));
+            for (int t = 0; t < len; ++t) {
+                C w = pbf[t];
+                C ph = pa[t];
+                pa[t] = mkc<C>(fma(R(2), w.x, -ph.x), fma(R(2), w.y, -ph.y));
+            }
+        } else {
+#pragma unroll 4
+            for (int t = 0; t < len; ++t) {
+                C w = pbf[t];
+                if (t >= tf) w = cfma(Co->pb[len - t - 1], wc, w);
+                C ph = pa[t];
+                pa[t] = mkc<C>(fma(R(2), w.x, -ph.x), fma(R(2), w.y, -ph.y));
+            }
         }
     }
-    __syncthreads();
+    // no CTA of the cluster may leave while its carries can still be read
+    group_sync(T);
 }
 
 __device__ __forceinline__ int sidx(const LineTiling& T, int lc, int k) { return lc * T.Lp + k + k / T.m; }
@@ -489,12 +563,14 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     C* sb = reinterpret_cast<C*>(smem_raw + T.off_b);
     C* cf = reinterpret_cast<C*>(smem_raw + T.off_cf);
     C* cb = reinterpret_cast<C*>(smem_raw + T.off_cb);
-    const int line0 = cta * T.R;
-    const int nl = min(T.R, T.nlines - line0);
+    const Part P = make_part(T, cta);
+    const int line0 = P.line0, nl = P.nl, Ll = P.len, k0 = P.k0;
     const int nx = A.nx, ny = A.ny, L = T.L;
     const size_t plane = (size_t)nx * ny;
-    // stage the CTA's rows psi[c][j][*] into sb (contiguous [r][c][i])
-    if (T.bulk && !stage_rows(sb, A.in, plane, line0, nl, L, &mbar, A.err)) return;
+    // stage the CTA's row segments psi[c][j][k0 .. k0 + Ll) into sb ([r][c][k] contiguous).
+    // If the bounded wait gives up (status bit set), the CTA still runs every
+    // barrier -- the other CTA of its cluster waits on them -- but writes nothing.
+    const bool ok = !(T.bulk && Ll > 0) || stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, &mbar, A.err);
 
     const double s = *A.scale;
     PConstT<R> k;
@@ -502,14 +578,18 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     k.dtc2 = R(A.dt * A.c2 * s * s);
     k.dtr = R(A.dt * A.rabi * 0.70710678118654752440);
     k.s = R(s);
-    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * L; e += T.threads) {
-        int r = e / L, i = e - r * L, j = line0 + r;
+    k.dt = R(A.dt);
+    // grid and trap constants in the pass precision (no FP64 work per site)
+    struct { R fx0, fdx, fy0, fdy, hx, hy; } tk = {R(A.x0), R(A.dx), R(A.y0), R(A.dy), R(0.5 * A.dt * A.wx * A.wx),
+                                                   R(0.5 * A.dt * A.wy * A.wy)};
+    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+        int r = e / Ll, kl = e - r * Ll, i = k0 + kl, j = line0 + r;
         C a, b, c;
         if (T.bulk) {
-            const C* row = sb + (size_t)r * 3 * L + i;
+            const C* row = sb + (size_t)r * 3 * Ll + kl;
             a = row[0];
-            b = row[L];
-            c = row[2 * L];
+            b = row[Ll];
+            c = row[2 * Ll];
         } else {
             size_t o = (size_t)j * nx + i;
             a = A.in[o];
@@ -517,9 +597,16 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
             c = A.in[2 * plane + o];
         }
         if (A.do_p) {
-            // the trap factor is real in imaginary time
-            C ev = MODE == 1 ? cmul(A.ex[i], A.ey[j]) : mkc<C>(A.ex[i].x * A.ey[j].x, R(0));
-            pointwise<MODE>(a, b, c, ev, k);
+            if constexpr (sizeof(R) == 8) {
+                // trap factor from the per-axis tables (real in imaginary time)
+                C ev = MODE == 1 ? cmul(A.ex[i], A.ey[j]) : mkc<C>(A.ex[i].x * A.ey[j].x, R(0));
+                pointwise<MODE>(a, b, c, ev, R(0), k);
+            } else {
+                // complex64: dt V joins the scalar exponent (no table loads)
+                const R xx = fma(R(i), tk.fdx, tk.fx0), yy = fma(R(j), tk.fdy, tk.fy0);
+                const R tv = fma(tk.hx * xx, xx, tk.hy * yy * yy);
+                pointwise<MODE>(a, b, c, mkc<C>(R(1), R(0)), tv, k);
+            }
         } else {
             a = mkc<C>(k.s * a.x, k.s * a.y);
             b = mkc<C>(k.s * b.x, k.s * b.y);
@@ -527,17 +614,18 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         }
         C p, z, m;
         to_sigma_y(a, b, c, p, z, m);
-        sa[sidx(T, r * 3 + 0, i)] = p;
-        sa[sidx(T, r * 3 + 1, i)] = z;
-        sa[sidx(T, r * 3 + 2, i)] = m;
+        sa[sidx(T, r * 3 + 0, kl)] = p;
+        sa[sidx(T, r * 3 + 1, kl)] = z;
+        sa[sidx(T, r * 3 + 2, kl)] = m;
     }
     __syncthreads();
-    if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, nl);
+    if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, P);
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
-    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * L; e += T.threads) {
-        int i = e / nl, r = e - i * nl, j = line0 + r;
+    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+        int kl = e / nl, r = e - kl * nl, i = k0 + kl, j = line0 + r;
         C xp, x0, xm;
-        sigma_y_to_x(sa[sidx(T, r * 3 + 0, i)], sa[sidx(T, r * 3 + 1, i)], sa[sidx(T, r * 3 + 2, i)], xp, x0, xm);
+        sigma_y_to_x(sa[sidx(T, r * 3 + 0, kl)], sa[sidx(T, r * 3 + 1, kl)], sa[sidx(T, r * 3 + 2, kl)], xp, x0, xm);
+        if (!ok) continue;
         size_t o = (size_t)i * ny + j;
         A.out[o] = xp;
         A.out[plane + o] = x0;
@@ -579,41 +667,64 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     C* sb = reinterpret_cast<C*>(smem_raw + T.off_b);
     C* cf = reinterpret_cast<C*>(smem_raw + T.off_cf);
     C* cb = reinterpret_cast<C*>(smem_raw + T.off_cb);
-    const int line0 = cta * T.R;
-    const int nl = min(T.R, T.nlines - line0);
+    const Part P = make_part(T, cta);
+    const int line0 = P.line0, nl = P.nl, Ll = P.len, k0 = P.k0;
     const int nx = A.nx, ny = A.ny, L = T.L;
     const size_t plane = (size_t)nx * ny;
-    // stage the CTA's rows t[mu][i][*] into sb (contiguous [r][mu][j])
-    if (T.bulk && !stage_rows(sb, A.in, plane, line0, nl, L, &mbar, A.err)) return;
+    // stage the CTA's row segments t[mu][i][k0 .. k0 + Ll) into sb ([r][mu][k] contiguous);
+    // on a timeout the CTA runs every barrier but writes nothing (see the x-pass)
+    const bool ok = !(T.bulk && Ll > 0) || stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, &mbar, A.err);
 
-    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * L; e += T.threads) {
-        int r = e / L, j = e - r * L, i = line0 + r;
+    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+        int r = e / Ll, kl = e - r * Ll, j = k0 + kl, i = line0 + r;
         if (T.bulk) {
-            const C* row = sb + (size_t)r * 3 * L + j;
-            sa[sidx(T, r * 3 + 0, j)] = row[0];
-            sa[sidx(T, r * 3 + 1, j)] = row[L];
-            sa[sidx(T, r * 3 + 2, j)] = row[2 * L];
+            const C* row = sb + (size_t)r * 3 * Ll + kl;
+            sa[sidx(T, r * 3 + 0, kl)] = row[0];
+            sa[sidx(T, r * 3 + 1, kl)] = row[Ll];
+            sa[sidx(T, r * 3 + 2, kl)] = row[2 * Ll];
         } else {
             size_t o = (size_t)i * ny + j;
-            sa[sidx(T, r * 3 + 0, j)] = A.in[o];
-            sa[sidx(T, r * 3 + 1, j)] = A.in[plane + o];
-            sa[sidx(T, r * 3 + 2, j)] = A.in[2 * plane + o];
+            sa[sidx(T, r * 3 + 0, kl)] = A.in[o];
+            sa[sidx(T, r * 3 + 1, kl)] = A.in[plane + o];
+            sa[sidx(T, r * 3 + 2, kl)] = A.in[2 * plane + o];
         }
     }
     __syncthreads();
-    if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, nl);
-    R acc = R(0);
-    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * L; e += T.threads) {
-        int j = e / nl, r = e - j * nl, i = line0 + r;
+    if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, P);
+    R acc = R(0), acc3[3] = {R(0), R(0), R(0)};
+    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+        int kl = e / nl, r = e - kl * nl, j = k0 + kl, i = line0 + r;
         C a, b, c;
-        from_sigma_x(sa[sidx(T, r * 3 + 0, j)], sa[sidx(T, r * 3 + 1, j)], sa[sidx(T, r * 3 + 2, j)], a, b, c);
+        from_sigma_x(sa[sidx(T, r * 3 + 0, kl)], sa[sidx(T, r * 3 + 1, kl)], sa[sidx(T, r * 3 + 2, kl)], a, b, c);
+        if (!ok) continue;
         size_t o = (size_t)j * nx + i;
         A.out[o] = a;
         A.out[plane + o] = b;
         A.out[2 * plane + o] = c;
-        acc += fma(a.x, a.x, a.y * a.y) + fma(b.x, b.x, b.y * b.y) + fma(c.x, c.x, c.y * c.y);
+        if (A.mcomp) {
+            acc3[0] += fma(a.x, a.x, a.y * a.y);
+            acc3[1] += fma(b.x, b.x, b.y * b.y);
+            acc3[2] += fma(c.x, c.x, c.y * c.y);
+        } else {
+            acc += fma(a.x, a.x, a.y * a.y) + fma(b.x, b.x, b.y * b.y) + fma(c.x, c.x, c.y * c.y);
+        }
     }
-    if (A.partials) {
+    if (A.partials && A.mcomp) {
+        // per-component partials (magnetisation-constrained normalisation)
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+        for (int cc = 0; cc < 3; ++cc) {
+            double dacc = (double)acc3[cc];
+            for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
+            if (lane == 0) wsum[warp] = dacc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int w = 0; w < nw; ++w) t += wsum[w];
+                A.partials[3 * cta + cc] = t;
+            }
+            __syncthreads();
+        }
+    } else if (A.partials) {
         double dacc = (double)acc;
         for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
         // threads past T.threads (batched launches) hold acc = 0: the sum is the
@@ -694,9 +805,25 @@ static int launch_pass(K kernel, const A& a, cudaStream_t st)
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.t.smem);
         if (e != cudaSuccess) return report_cuda(e, "cudaFuncSetAttribute(line pass)");
     }
-    int grid = (a.t.nlines + a.t.R - 1) / a.t.R;
-    kernel<<<grid, a.t.threads, a.t.smem, st>>>(a);
-    return report_cuda(cudaGetLastError(), "line pass launch");
+    const int grid = (a.t.nlines + a.t.R - 1) / a.t.R * a.t.S;
+    if (a.t.S == 1) {
+        kernel<<<grid, a.t.threads, a.t.smem, st>>>(a);
+        return report_cuda(cudaGetLastError(), "line pass launch");
+    }
+    // a line group spans a cluster of S CTAs
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(a.t.threads);
+    cfg.dynamicSmemBytes = a.t.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = a.t.S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return report_cuda(cudaLaunchKernelEx(&cfg, kernel, a), "line pass cluster launch");
 }
 
 int launch_xpass(const PassArgs& a, int mode, cudaStream_t st)

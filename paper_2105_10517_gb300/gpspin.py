@@ -32,7 +32,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-           "gp_init_winding", "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step",
+           "gp_init_winding", "gp_set_magnetization", "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_strerror"]
 
@@ -142,11 +142,15 @@ def load():
     lib.gp_init_gaussian.argtypes = [vp, dp, ctypes.c_ulonglong, ctypes.c_double]
     lib.gp_init_winding.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.c_ulonglong, ctypes.c_double]
     lib.gp_init_winding.restype = ctypes.c_int
+    lib.gp_set_magnetization.argtypes = [vp, ip, ctypes.c_double]
+    lib.gp_set_magnetization.restype = ctypes.c_int
     lib.gp_propagate.argtypes = [vp, ctypes.c_longlong, ip]
     lib.gp_refine_fp64.argtypes = [vp, ctypes.c_longlong, ip]
     lib.gp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
     lib.gp_apply_substep.argtypes = [vp, ip, ip]
     lib.gp_profile_step.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_float)]
+    lib.gp_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double)]
+    lib.gp_autotune.restype = ctypes.c_int
     lib.gp_propagate_noalloc.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_longlong, ip, vp]
     lib.gp_propagate_noalloc.restype = ctypes.c_int
     lib.gp_request_bytes.argtypes = [ctypes.POINTER(Params), ip]
@@ -278,6 +282,11 @@ class Solver:
         w = (ctypes.c_int * 3)(*[int(v) for v in winding])
         _check(load().gp_init_winding(self._h, _dptr(f), w, int(seed), float(phase_noise)), "gp_init_winding")
 
+    def set_magnetization(self, m):
+        """Keep N = 1 and N+ - N- = m in imaginary time (None: plain renormalisation)."""
+        _check(load().gp_set_magnetization(self._h, 0 if m is None else 1, 0.0 if m is None else float(m)),
+               "gp_set_magnetization")
+
     def propagate(self, nsteps, mode=IMAG):
         _check(load().gp_propagate(self._h, int(nsteps), int(mode)), "gp_propagate")
 
@@ -294,6 +303,12 @@ class Solver:
         ms = (ctypes.c_float * 4)()
         _check(load().gp_profile_step(self._h, int(mode), ms), "gp_profile_step")
         return list(ms)
+
+    def autotune(self, mode=IMAG):
+        """Pick the fastest tiling of both line passes (state unchanged); returns their ms."""
+        ms = ctypes.c_double()
+        _check(load().gp_autotune(self._h, int(mode), ctypes.byref(ms)), "gp_autotune")
+        return ms.value
 
     def observables(self):
         o = Obs()

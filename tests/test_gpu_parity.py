@@ -231,3 +231,43 @@ def test_graph_replay_matches_direct_launches(mode):
                 s.propagate(n, mode)
             out.append(s.get_state())
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("mode", [IMAG, REAL])
+@pytest.mark.parametrize("shape", [(300, 270), (301, 257)])
+def test_long_lines_split_over_a_cluster(shape, mode):
+    """Lines of >= 256 points span a 2-CTA cluster (carries through distributed
+    shared memory); odd lengths also take the unstaged load path."""
+    nx, ny = shape
+    p = ragged(nx=nx, ny=ny, xlen=0.05 * nx, ylen=0.05 * ny, dt=0.0005)
+    psi = smooth_plus_rough(p, 51)
+    want = oracle.propagate(p, psi, 2, mode)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        s.propagate(2, mode)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+    with gpspin.Solver(dict(p, precision=gpspin.FP32_MIXED)) as s:
+        s.set_state(psi)
+        s.propagate(2, mode)
+        got32 = s.get_state()
+    assert np.max(np.abs(got32 - want)) <= 4e-6 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("precision", [gpspin.FP64, gpspin.FP32_MIXED])
+def test_autotune_keeps_state_and_results(precision):
+    """gp_autotune times candidate tilings without changing the state; propagation
+    with the tuned tilings agrees with the oracle."""
+    p = ragged(nx=288, ny=264, xlen=0.05 * 288, ylen=0.05 * 264, dt=0.0005, precision=precision)
+    psi = smooth_plus_rough(p, 61)
+    want = oracle.propagate(p, psi, 3, IMAG)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        before = s.get_state()
+        ms = s.autotune(IMAG)
+        assert ms > 0
+        assert np.array_equal(s.get_state(), before)
+        s.propagate(3, IMAG)
+        got = s.get_state()
+    tol = 1e-12 if precision == gpspin.FP64 else 4e-6
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))

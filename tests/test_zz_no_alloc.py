@@ -19,11 +19,12 @@ def params():
                 gamma=0.7, rabi=0.3)
 
 
+@pytest.mark.parametrize("shape", [(200, 120), (256, 256)])
 @pytest.mark.parametrize("mode", [gpspin.IMAG, gpspin.REAL])
-def test_noalloc_matches_propagate_twice(mode):
+def test_noalloc_matches_propagate_twice(mode, shape):
     import torch
     gpspin.build()
-    p = params()
+    p = dict(params(), nx=shape[0], ny=shape[1], xlen=0.1 * shape[0], ylen=0.1 * shape[1])
     psi0 = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=13) \
         + inputs.random_state(p["nx"], p["ny"], seed=14, scale=0.02)
     stream = torch.cuda.Stream()
