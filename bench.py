@@ -205,6 +205,7 @@ def run_ours(args):
     tuned_ms = None
     if not args.no_autotune:
         tuned_ms = s.autotune(mode)  # untimed; the state is unchanged
+    tiles = s.tiling(mode)
     for _ in range(max(3, args.warmup)):
         s.profile_step(mode)
 
@@ -219,10 +220,12 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     per = []
+    torch.cuda.nvtx.range_push("bench_timed")  # ncu --nvtx --nvtx-include "bench_timed/"
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         per.append(s.profile_step(mode))
+    torch.cuda.nvtx.range_pop()
     barrier()
     wall = time.perf_counter() - t0
     # keep the GPU busy until the sampler has seen the load a few times
@@ -305,7 +308,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic (seeded Gaussian + splitmix64 phase noise)",
-            "config": dict(config_dict(c, name, prec), tiling="default" if tuned_ms is None else "autotuned"),
+            "config": dict(config_dict(c, name, prec), tiling="default" if tuned_ms is None else "autotuned",
+                           tiles=tiles),
             "roofline": roofline, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "clocks": clocks.summary(), "wall_s_timed_loop": wall,
         }

@@ -214,13 +214,28 @@ int gp_batch_poll(gp_batch* b, long long id, int* state, long long* steps, gp_ob
 
 /* Autotuner: for the handle's current precision and the given mode, times the
  * x-pass and the y-pass for each candidate tiling -- lines per CTA (1, 2, 4),
- * one CTA or a 2-CTA cluster per line group, chunk lengths of the parallel
+ * one CTA or a cluster of 2, 4 or 8 CTAs per line group, chunk lengths of the parallel
  * Thomas solve -- on the handle's stream, and keeps the fastest for later
  * propagation.  The state is saved and restored, so tuning does not change the
  * solve; results stay within the parity tolerances (only the summation order of
  * partial norms and the chunking change).  *ms_out (may be NULL) receives the
  * tuned x-pass + y-pass time.  Allocates one temporary copy of psi. */
 int gp_autotune(gp_handle* h, int mode, double* ms_out);
+
+/* Sets the tiling of one pass (dir 0: x-pass, 1: y-pass) for the handle's current
+ * precision and the given mode: cluster = CTAs per line group (1, 2, 4 or 8),
+ * lines_per_cta, chunk = minimum chunk length of the parallel Thomas solve
+ * (raised to what the precision needs).  GP_ERR_ARG or GP_ERR_UNSUPPORTED if
+ * the tiling does not fit (threads, shared memory, chunks per CTA).  Results
+ * stay within the parity tolerances for every valid tiling. */
+int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk);
+
+/* The tiling the handle uses for a pass (dir 0: x-pass, 1: y-pass) in the given
+ * mode and its current precision: out[0] CTAs per line group (cluster size),
+ * out[1] lines per CTA, out[2] chunk length, out[3] chunks per line, out[4]
+ * threads per CTA, out[5] dynamic shared memory bytes, out[6] CTAs per launch.
+ * out must hold 7 ints. */
+int gp_tiling_info(gp_handle* h, int mode, int dir, int* out);
 
 /* Human-readable text for a gp_status. */
 const char* gp_strerror(int status);

@@ -78,7 +78,7 @@ double max_cp(const gp_params& p, int dir, int mode)
 int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_req, LineTiling* t)
 {
     if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
-    if (S < 1 || S > 2 || R < 1) return GP_ERR_ARG;
+    if (S < 1 || S > 8 || (S & (S - 1)) || R < 1) return GP_ERR_ARG;  // portable cluster sizes
     const double bits = fp32 ? 26.0 : 60.0;
     const size_t elem = fp32 ? sizeof(float2) : sizeof(double2);
     int F = cpmax > 0 ? (int)std::ceil(bits * std::log(2.0) / -std::log(cpmax)) + 1 : 1;
@@ -87,7 +87,7 @@ int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_r
     int m = std::max(std::max(16, H + F), m_req);
     m = (m + 3) / 4 * 4;
     int Q = (L + m - 1) / m;
-    if (S > 1 && Q < 4) return GP_ERR_ARG;
+    if (S > 1 && Q < 2 * S) return GP_ERR_ARG;  // at least two chunks per CTA
     const int Qc = (Q + S - 1) / S;
     const int Lp = Qc * (m + 1) + 1;
     if (3 * R * Qc > 512 || R > nlines) return GP_ERR_ARG;
@@ -759,7 +759,7 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
         LineTiling best = cur;
         float best_ms = -1.0f;
         const int ms_add[] = {0, 4, 8, 16, 32};
-        for (int S = 1; S <= 2; ++S)
+        for (int S : {1, 2, 4, 8})
             for (int R : {1, 2, 4})
                 for (int add : ms_add) {
                     LineTiling t;
@@ -794,6 +794,41 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
     drop_graphs(h);
     if (ms_out) *ms_out = best_total;
     return st;
+}
+
+int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk)
+{
+    if (!h || (mode != GP_IMAG && mode != GP_REAL) || dir < 0 || dir > 1) return GP_ERR_ARG;
+    int st = ensure_coef(h, mode);
+    if (st) return st;
+    CoefSet& cs = h->coef[mode];
+    const gp_params& p = h->p;
+    const bool f32 = h->active == GP_FP32_MIXED;
+    LineTiling t;
+    st = make_tiling(dir == 0 ? p.nx : p.ny, dir == 0 ? p.ny : p.nx, max_cp(p, dir, mode), f32, cluster,
+                     lines_per_cta, chunk, &t);
+    if (st) return st;
+    (f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty)) = t;
+    drop_graphs(h);
+    return GP_OK;
+}
+
+int gp_tiling_info(gp_handle* h, int mode, int dir, int* out)
+{
+    if (!h || !out || (mode != GP_IMAG && mode != GP_REAL) || dir < 0 || dir > 1) return GP_ERR_ARG;
+    int st = ensure_coef(h, mode);
+    if (st) return st;
+    const CoefSet& cs = h->coef[mode];
+    const bool f32 = h->active == GP_FP32_MIXED;
+    const LineTiling& t = f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty);
+    out[0] = t.S;
+    out[1] = t.R;
+    out[2] = t.m;
+    out[3] = t.Q;
+    out[4] = t.threads;
+    out[5] = (int)t.smem;
+    out[6] = y_blocks(t);
+    return GP_OK;
 }
 
 int gp_apply_substep(gp_handle* h, int which, int mode)

@@ -572,16 +572,30 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     // barrier -- the other CTA of its cluster waits on them -- but writes nothing.
     const bool ok = !(T.bulk && Ll > 0) || stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, &mbar, A.err);
 
-    const double s = *A.scale;
-    PConstT<R> k;
-    k.dtc0 = R(A.dt * A.c0 * s * s);
-    k.dtc2 = R(A.dt * A.c2 * s * s);
-    k.dtr = R(A.dt * A.rabi * 0.70710678118654752440);
-    k.s = R(s);
-    k.dt = R(A.dt);
-    // grid and trap constants in the pass precision (no FP64 work per site)
-    struct { R fx0, fdx, fy0, fdy, hx, hy; } tk = {R(A.x0), R(A.dx), R(A.y0), R(A.dy), R(0.5 * A.dt * A.wx * A.wx),
-                                                   R(0.5 * A.dt * A.wy * A.wy)};
+    // Per-CTA constants, computed once by thread 0 (FP64 work is costly on this
+    // part even inside the complex64 pass) and broadcast through shared memory.
+    struct KC {
+        PConstT<R> k;
+        R fx0, fdx, fy0, fdy, hx, hy;  // grid and trap constants (complex64 pass)
+    };
+    __shared__ KC kc;
+    if (threadIdx.x == 0) {
+        const double s = *A.scale;
+        kc.k.dtc0 = R(A.dt * A.c0 * s * s);
+        kc.k.dtc2 = R(A.dt * A.c2 * s * s);
+        kc.k.dtr = R(A.dt * A.rabi * 0.70710678118654752440);
+        kc.k.s = R(s);
+        kc.k.dt = R(A.dt);
+        kc.fx0 = R(A.x0);
+        kc.fdx = R(A.dx);
+        kc.fy0 = R(A.y0);
+        kc.fdy = R(A.dy);
+        kc.hx = R(0.5 * A.dt * A.wx * A.wx);
+        kc.hy = R(0.5 * A.dt * A.wy * A.wy);
+    }
+    __syncthreads();
+    const PConstT<R> k = kc.k;
+    const struct { R fx0, fdx, fy0, fdy, hx, hy; } tk = {kc.fx0, kc.fdx, kc.fy0, kc.fdy, kc.hx, kc.hy};
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int r = e / Ll, kl = e - r * Ll, i = k0 + kl, j = line0 + r;
         C a, b, c;
@@ -713,9 +727,9 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
         // per-component partials (magnetisation-constrained normalisation)
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
         for (int cc = 0; cc < 3; ++cc) {
-            double dacc = (double)acc3[cc];
-            for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
-            if (lane == 0) wsum[warp] = dacc;
+            R racc = acc3[cc];
+            for (int off = 16; off > 0; off >>= 1) racc += __shfl_xor_sync(0xffffffffu, racc, off);
+            if (lane == 0) wsum[warp] = (double)racc;
             __syncthreads();
             if (threadIdx.x == 0) {
                 double t = 0.0;
@@ -725,8 +739,10 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
             __syncthreads();
         }
     } else if (A.partials) {
-        double dacc = (double)acc;
-        for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
+        // warp sums in the pass precision, widened once per warp, CTA sum in FP64
+        R racc = acc;
+        for (int off = 16; off > 0; off >>= 1) racc += __shfl_xor_sync(0xffffffffu, racc, off);
+        double dacc = (double)racc;
         // threads past T.threads (batched launches) hold acc = 0: the sum is the
         // same as in a launch of exactly T.threads threads
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;

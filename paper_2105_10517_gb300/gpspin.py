@@ -33,6 +33,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
            "gp_init_winding", "gp_set_magnetization", "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
+           "gp_tiling_info", "gp_set_tiling",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_strerror"]
 
@@ -151,6 +152,10 @@ def load():
     lib.gp_profile_step.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_float)]
     lib.gp_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_double)]
     lib.gp_autotune.restype = ctypes.c_int
+    lib.gp_tiling_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
+    lib.gp_tiling_info.restype = ctypes.c_int
+    lib.gp_set_tiling.argtypes = [vp, ip, ip, ip, ip, ip]
+    lib.gp_set_tiling.restype = ctypes.c_int
     lib.gp_propagate_noalloc.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_longlong, ip, vp]
     lib.gp_propagate_noalloc.restype = ctypes.c_int
     lib.gp_request_bytes.argtypes = [ctypes.POINTER(Params), ip]
@@ -309,6 +314,21 @@ class Solver:
         ms = ctypes.c_double()
         _check(load().gp_autotune(self._h, int(mode), ctypes.byref(ms)), "gp_autotune")
         return ms.value
+
+    def set_tiling(self, dir, cluster=1, lines_per_cta=1, chunk=0, mode=IMAG):
+        """Force the tiling of the x-pass (dir 0) or y-pass (dir 1)."""
+        _check(load().gp_set_tiling(self._h, int(mode), int(dir), int(cluster), int(lines_per_cta), int(chunk)),
+               "gp_set_tiling")
+
+    def tiling(self, mode=IMAG):
+        """Tiling of the x- and y-pass: dicts of cluster size, lines per CTA, chunk length..."""
+        out = {}
+        for d, name in ((0, "xpass"), (1, "ypass")):
+            v = (ctypes.c_int * 7)()
+            _check(load().gp_tiling_info(self._h, int(mode), d, v), "gp_tiling_info")
+            out[name] = dict(cluster=v[0], lines_per_cta=v[1], chunk=v[2], chunks=v[3], threads=v[4], smem=v[5],
+                             ctas=v[6])
+        return out
 
     def observables(self):
         o = Obs()

@@ -271,3 +271,24 @@ def test_autotune_keeps_state_and_results(precision):
         got = s.get_state()
     tol = 1e-12 if precision == gpspin.FP64 else 4e-6
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+@pytest.mark.parametrize("precision", [gpspin.FP64, gpspin.FP32_MIXED])
+def test_every_cluster_size(cluster, precision):
+    """Line groups spread over 1, 2, 4 or 8 CTAs of a cluster (carries through
+    distributed shared memory) all give the oracle's result."""
+    # 16 chunks per line at the least for a cluster of 8 (two per CTA)
+    p = ragged(nx=640, ny=608, xlen=0.05 * 640, ylen=0.05 * 608, dt=0.0005, precision=precision)
+    psi = smooth_plus_rough(p, 71)
+    want = oracle.propagate(p, psi, 2, IMAG)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        for d in (0, 1):
+            s.set_tiling(d, cluster=cluster, lines_per_cta=2 if cluster < 8 else 1, chunk=24)
+        t = s.tiling()
+        assert t["xpass"]["cluster"] == cluster and t["ypass"]["cluster"] == cluster
+        s.propagate(2, IMAG)
+        got = s.get_state()
+    tol = 1e-12 if precision == gpspin.FP64 else 4e-6
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
