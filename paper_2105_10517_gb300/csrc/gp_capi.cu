@@ -75,6 +75,25 @@ double max_cp(const gp_params& p, int dir, int mode)
 // with H the rows until the factorisation has converged (contraction |c'|^2
 // per row); R lines per CTA within ~100 KB of shared memory (two CTAs per SM)
 // and 512 threads.
+// Bank conflicts of the solve's chunk-parallel shared-memory accesses: thread
+// tid = ql * nl3 + lc reads element lc * Lp + ql * cs + t, and the threads of each
+// group of G (G = 128 bytes / element size, one shared-memory wavefront) should
+// fall on distinct banks, i.e. differ modulo G.  Returns the extra wavefronts.
+static int solve_conflicts(int cs, int Lp, int nl3, int Qc, int G)
+{
+    const int n = nl3 * Qc;
+    int extra = 0;
+    for (int g0 = 0; g0 < n; g0 += G) {
+        int cnt[16] = {0}, mx = 0;
+        for (int tid = g0; tid < std::min(n, g0 + G); ++tid) {
+            const int ql = tid / nl3, lc = tid - ql * nl3;
+            mx = std::max(mx, ++cnt[(lc * Lp + ql * cs) % G]);
+        }
+        extra += mx - 1;
+    }
+    return extra;
+}
+
 int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_req, LineTiling* t)
 {
     if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
@@ -86,11 +105,24 @@ int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_r
     if (F > kFix || H > kHead) return GP_ERR_UNSUPPORTED;
     int m = std::max(std::max(16, H + F), m_req);
     m = (m + 3) / 4 * 4;
+    if (fp32 && m <= 32) m = m <= 16 ? 16 : (m <= 24 ? 24 : 32);  // the register-resident solves
     int Q = (L + m - 1) / m;
     if (S > 1 && Q < 2 * S) return GP_ERR_ARG;  // at least two chunks per CTA
     const int Qc = (Q + S - 1) / S;
-    const int Lp = Qc * (m + 1) + 1;
     if (3 * R * Qc > 512 || R > nlines) return GP_ERR_ARG;
+    // strides: fewest bank conflicts, then least shared memory
+    const int G = fp32 ? 16 : 8;
+    int cs = m, Lp = Qc * m, best = -1;
+    for (int dc = 0; dc < G; ++dc)
+        for (int dl = 0; dl < G; ++dl) {
+            const int c = m + dc, l = Qc * c + dl;
+            const int k = solve_conflicts(c, l, 3 * R, Qc, G);
+            if (best < 0 || k < best || (k == best && l < Lp)) {
+                best = k;
+                cs = c;
+                Lp = l;
+            }
+        }
     auto up = [](size_t b) { return (b + 127) / 128 * 128; };
     const size_t smem = up(3 * R * Lp * elem) * 2 + 2 * up(3 * R * Qc * elem);
     if (smem > 227 * 1024) return GP_ERR_UNSUPPORTED;
@@ -102,6 +134,7 @@ int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_r
     t->S = S;
     t->Qc = Qc;
     t->F = std::min(F, m - 1);
+    t->cs = cs;
     t->Lp = Lp;
     t->threads = std::min(512, (std::max(32, 3 * R * Qc) + 31) / 32 * 32);
     t->smem = smem;

@@ -61,7 +61,9 @@ struct LineTiling {
     int m;      // chunk length of the parallel Thomas solve
     int Q;      // chunks per line = ceil(L / m)
     int F;      // fixup length (|c'_inf|^F below the precision's rounding), F < m
-    int Lp;     // padded smem stride of one line-channel in a CTA: Qc (m + 1) + 1
+    int cs;     // smem stride of one chunk (>= m; the padding spreads the chunk-parallel
+                // accesses of the solve over the banks)
+    int Lp;     // smem stride of one line-channel in a CTA (>= Qc cs)
     int S;      // CTAs per line group (a thread-block cluster when S > 1)
     int Qc;     // chunks per CTA = ceil(Q / S); CTA rank r holds chunks r*Qc ..
     int threads;

@@ -442,25 +442,25 @@ __device__ __forceinline__ void from_sigma_x(C xp, C x0, C xm, C& a, C& b, C& c)
 //     the chunk's last F points.
 // Because m > F, a chunk's local end/start value equals the true one to
 // rounding, so no carry has to be propagated sequentially across chunks.
-// Smem: line-channel arrays of stride Lp, chunk q at offset q (m + 1) (the pad
-// keeps chunk-parallel accesses on distinct banks).
+// Smem: line-channel arrays of stride Lp, chunk q at offset q cs (the strides
+// keep chunk-parallel accesses on distinct banks).
 template <typename C>
 __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const LineCoefT<C>* coef,
                                                const LineTiling& T, const Part& P)
 {
     typedef typename RealOf<C>::type R;
     const int m = T.m, Q = T.Q, F = T.F, L = T.L, Lp = T.Lp, Qc = T.Qc;
-    const int nthr = 3 * P.nl * Qc;
+    const int nl3 = 3 * max(P.nl, 1);
     const int tid = threadIdx.x;
-    const int ql = tid % Qc;               // chunk within the CTA
-    const int lc = min(tid / Qc, 3 * max(P.nl, 1) - 1);  // r * 3 + ch
-    const bool active = tid < nthr && ql < P.nq;
+    const int ql = tid / nl3;              // chunk within the CTA (chunk-major: the
+    const int lc = tid - ql * nl3;         // line-start chunks sit in the first warp); r * 3 + ch
+    const bool active = ql < P.nq;
     const int q = P.q0 + ql;               // chunk within the line
     const int start = q * m;
     const int len = max(0, min(m, L - start));
     const LineCoefT<C>* Co = coef + lc;    // coef already offset to the CTA's first line
-    C* __restrict__ pa = sa + lc * Lp + ql * (m + 1);
-    C* __restrict__ pbf = sb + lc * Lp + ql * (m + 1);
+    C* __restrict__ pa = sa + lc * Lp + ql * T.cs;
+    C* __restrict__ pbf = sb + lc * Lp + ql * T.cs;
     // carries of the neighbouring CTAs of the cluster (distributed shared memory)
     const C* cf_prev = cf;
     const C* cb_next = cb;
@@ -550,11 +550,163 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
     group_sync(T);
 }
 
-__device__ __forceinline__ int sidx(const LineTiling& T, int lc, int k) { return lc * T.Lp + k + k / T.m; }
+// The same solve with the chunk length M fixed at compile time and each
+// thread's chunk of y / w held in registers: shared memory is read for phi in
+// the forward sweep and in the final step and written once with psi'.
+// Chunks q >= 1 start at row m >= H + F, past the rows where the factorisation
+// still differs from its limit (H rows) and where the fixup powers matter, so
+// they use the converged coefficients throughout; chunk 0 takes the table rows.
+template <typename C, int M>
+__device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const LineCoefT<C>* coef,
+                                                   const LineTiling& T, const Part& P)
+{
+    typedef typename RealOf<C>::type R;
+    const int Q = T.Q, F = T.F, L = T.L, Lp = T.Lp, Qc = T.Qc;
+    const int nl3 = 3 * max(P.nl, 1);
+    const int tid = threadIdx.x;
+    const int ql = tid / nl3;
+    const int lc = tid - ql * nl3;
+    const bool active = ql < P.nq;
+    const int q = P.q0 + ql;
+    const int len = max(0, min(M, L - q * M));
+    const LineCoefT<C>* Co = coef + lc;
+    C* __restrict__ pa = sa + lc * Lp + ql * T.cs;
+    const C* cf_prev = cf;
+    const C* cb_next = cb;
+    if (T.S > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        if (P.rank > 0) cf_prev = cl.map_shared_rank(cf, P.rank - 1);
+        if (P.rank < T.S - 1) cb_next = cl.map_shared_rank(cb, P.rank + 1);
+    }
+    const C zero = mkc<C>(R(0), R(0));
+    const C inv_c = Co->inv[kHead - 1], g_c = Co->g[kHead - 1], cp_c = Co->cp[kHead - 1];
+    C y[M];
+    if (active) {
+        // forward elimination from a zero carry; rows past the line end stay zero
+        C v = zero;
+        if (q == 0) {
+#pragma unroll
+            for (int t = 0; t < M; ++t) {
+                const int k = t < kHead - 1 ? t : kHead - 1;
+                v = cfnma(Co->g[k], v, cmul(Co->inv[k], pa[t]));
+                y[t] = t < len ? v : zero;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < M; ++t) {
+                v = cfnma(g_c, v, cmul(inv_c, pa[t]));
+                y[t] = t < len ? v : zero;
+            }
+        }
+        cf[lc * Qc + ql] = y[M - 1];
+    }
+    group_sync(T);
+    if (active) {
+        if (q > 0) {
+            const C yc = ql > 0 ? cf[lc * Qc + ql - 1] : cf_prev[lc * Qc + Qc - 1];
+            const int nf = min(F, len);
+            if constexpr (sizeof(R) == 4) {
+                const C mg = mkc<C>(-g_c.x, -g_c.y);
+                C pw = mg;
+#pragma unroll
+                for (int t = 0; t < M; ++t) {
+                    if (t < nf) {
+                        y[t] = cfma(pw, yc, y[t]);
+                        pw = cmul(pw, mg);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < M; ++t)
+                    if (t < nf) y[t] = cfma(Co->pf[t], yc, y[t]);
+            }
+        }
+        // back substitution from a zero carry
+        C w = zero;
+        if (q == 0) {
+#pragma unroll
+            for (int t = M - 1; t >= 0; --t) {
+                const int k = t < kHead - 1 ? t : kHead - 1;
+                w = cfnma(Co->cp[k], w, y[t]);
+                y[t] = w;
+            }
+        } else {
+#pragma unroll
+            for (int t = M - 1; t >= 0; --t) {
+                w = cfnma(cp_c, w, y[t]);
+                y[t] = w;
+            }
+        }
+        cb[lc * Qc + ql] = y[0];
+    }
+    group_sync(T);
+    if (active) {
+        if (q < Q - 1) {  // full chunk (len == M): the last F points take the backward fixup
+            const C wc = ql < P.nq - 1 ? cb[lc * Qc + ql + 1] : cb_next[lc * Qc + 0];
+            if constexpr (sizeof(R) == 4) {
+                const C mc = mkc<C>(-cp_c.x, -cp_c.y);
+                C pw = mc;
+#pragma unroll
+                for (int t = M - 1; t >= 0; --t) {
+                    if (t >= M - F) {
+                        y[t] = cfma(pw, wc, y[t]);
+                        pw = cmul(pw, mc);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = M - 1; t >= 0; --t)
+                    if (t >= M - F) y[t] = cfma(Co->pb[M - 1 - t], wc, y[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < M; ++t) {
+            if (t < len) {
+                const C ph = pa[t];
+                pa[t] = mkc<C>(fma(R(2), y[t].x, -ph.x), fma(R(2), y[t].y, -ph.y));
+            }
+        }
+    }
+    // no CTA of the cluster may leave while its carries can still be read
+    group_sync(T);
+}
+
+// Solve of the CTA's lines: the register-resident form when the kernel is
+// compiled for the tiling's chunk length M, the shared-memory form for M = 0.
+template <typename C, int M>
+__device__ __forceinline__ void solve_lines(C* sa, C* sb, C* cf, C* cb, const LineCoefT<C>* coef,
+                                            const LineTiling& T, const Part& P)
+{
+    if constexpr (M > 0)
+        chunked_thomas_reg<C, M>(sa, cf, cb, coef, T, P);
+    else
+        chunked_thomas(sa, sb, cf, cb, coef, T, P);
+}
+
+// Division by a per-CTA constant d as a multiply-high: q = floor(k * ceil(2^32 / d) / 2^32)
+// is exact for 0 <= k < 2^32 / d (the rounding-up error of the multiplier adds
+// less than k / 2^32 < 1/d to k/d).  A CTA's shared memory holds fewer than
+// 2^13 line points, so every index k and divisor d of a pass satisfies k d < 2^26.
+struct FastDiv {
+    uint32_t mul;  // ceil(2^32 / d); 0 encodes d == 1
+    __device__ __forceinline__ explicit FastDiv(int d) : mul(d > 1 ? 0xffffffffu / (uint32_t)d + 1u : 0u) {}
+    __device__ __forceinline__ int operator()(int k) const
+    {
+        return mul ? (int)__umulhi((uint32_t)k, mul) : k;
+    }
+};
+
+// shared-memory position of line point k: chunk k / m at offset (k / m) cs
+struct SPos {
+    FastDiv dm;
+    int pad;  // cs - m
+    __device__ __forceinline__ explicit SPos(const LineTiling& T) : dm(T.m), pad(T.cs - T.m) {}
+    __device__ __forceinline__ int operator()(int k) const { return k + dm(k) * pad; }
+};
 
 // --------------------------------------------------------------- x-pass ----
 // One CTA of the x-pass: lines cta*R .. cta*R + R - 1 of instance A.
-template <int MODE, typename C>
+template <int MODE, typename C, int M>
 __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar)
 {
     typedef typename RealOf<C>::type R;
@@ -596,8 +748,11 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     __syncthreads();
     const PConstT<R> k = kc.k;
     const struct { R fx0, fdx, fy0, fdy, hx, hy; } tk = {kc.fx0, kc.fdx, kc.fy0, kc.fdy, kc.hx, kc.hy};
+    const FastDiv div_len(Ll), div_nl(nl);
+    const SPos spos(T);
+    const int Lp = T.Lp;
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
-        int r = e / Ll, kl = e - r * Ll, i = k0 + kl, j = line0 + r;
+        int r = div_len(e), kl = e - r * Ll, i = k0 + kl, j = line0 + r;
         C a, b, c;
         if (T.bulk) {
             const C* row = sb + (size_t)r * 3 * Ll + kl;
@@ -628,17 +783,19 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         }
         C p, z, m;
         to_sigma_y(a, b, c, p, z, m);
-        sa[sidx(T, r * 3 + 0, kl)] = p;
-        sa[sidx(T, r * 3 + 1, kl)] = z;
-        sa[sidx(T, r * 3 + 2, kl)] = m;
+        C* dst = sa + r * 3 * Lp + spos(kl);
+        dst[0] = p;
+        dst[Lp] = z;
+        dst[2 * Lp] = m;
     }
     __syncthreads();
-    if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, P);
+    if (A.do_solve) solve_lines<C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, P);
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
-        int kl = e / nl, r = e - kl * nl, i = k0 + kl, j = line0 + r;
+        int kl = div_nl(e), r = e - kl * nl, i = k0 + kl, j = line0 + r;
         C xp, x0, xm;
-        sigma_y_to_x(sa[sidx(T, r * 3 + 0, kl)], sa[sidx(T, r * 3 + 1, kl)], sa[sidx(T, r * 3 + 2, kl)], xp, x0, xm);
+        const C* src = sa + r * 3 * Lp + spos(kl);
+        sigma_y_to_x(src[0], src[Lp], src[2 * Lp], xp, x0, xm);
         if (!ok) continue;
         size_t o = (size_t)i * ny + j;
         A.out[o] = xp;
@@ -647,12 +804,13 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     }
 }
 
-template <int MODE, typename C>
+// M: chunk length of a register-resident solve, 0 for the shared-memory solve
+template <int MODE, typename C, int M>
 __global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
-    xpass_body<MODE, C>(A, blockIdx.x, smem_raw, mbar);
+    xpass_body<MODE, C, M>(A, blockIdx.x, smem_raw, mbar);
 }
 
 // Many instances in one launch: CTA b works on item items[b] = (instance, cta)
@@ -665,13 +823,13 @@ __global__ void __launch_bounds__(512) xpass_batched(const PassArgsT<C>* args, c
     if ((int)blockIdx.x >= *n_items) return;
     const int2 it = items[blockIdx.x];
     const PassArgsT<C> A = args[it.x];
-    xpass_body<MODE, C>(A, it.y, smem_raw, mbar);
+    xpass_body<MODE, C, 0>(A, it.y, smem_raw, mbar);
 }
 
 // --------------------------------------------------------------- y-pass ----
 // Partial norms: each thread sums its sites' |psi|^2 in the pass's precision
 // (a few dozen sites), the CTA then adds the threads' sums in FP64.
-template <int MODE, typename C>
+template <int MODE, typename C, int M>
 __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar,
                                            double* wsum)
 {
@@ -689,27 +847,32 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     // on a timeout the CTA runs every barrier but writes nothing (see the x-pass)
     const bool ok = !(T.bulk && Ll > 0) || stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, &mbar, A.err);
 
+    const FastDiv div_len(Ll), div_nl(nl);
+    const SPos spos(T);
+    const int Lp = T.Lp;
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
-        int r = e / Ll, kl = e - r * Ll, j = k0 + kl, i = line0 + r;
+        int r = div_len(e), kl = e - r * Ll, j = k0 + kl, i = line0 + r;
+        C* dst = sa + r * 3 * Lp + spos(kl);
         if (T.bulk) {
             const C* row = sb + (size_t)r * 3 * Ll + kl;
-            sa[sidx(T, r * 3 + 0, kl)] = row[0];
-            sa[sidx(T, r * 3 + 1, kl)] = row[Ll];
-            sa[sidx(T, r * 3 + 2, kl)] = row[2 * Ll];
+            dst[0] = row[0];
+            dst[Lp] = row[Ll];
+            dst[2 * Lp] = row[2 * Ll];
         } else {
             size_t o = (size_t)i * ny + j;
-            sa[sidx(T, r * 3 + 0, kl)] = A.in[o];
-            sa[sidx(T, r * 3 + 1, kl)] = A.in[plane + o];
-            sa[sidx(T, r * 3 + 2, kl)] = A.in[2 * plane + o];
+            dst[0] = A.in[o];
+            dst[Lp] = A.in[plane + o];
+            dst[2 * Lp] = A.in[2 * plane + o];
         }
     }
     __syncthreads();
-    if (A.do_solve) chunked_thomas(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, P);
+    if (A.do_solve) solve_lines<C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, P);
     R acc = R(0), acc3[3] = {R(0), R(0), R(0)};
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
-        int kl = e / nl, r = e - kl * nl, j = k0 + kl, i = line0 + r;
+        int kl = div_nl(e), r = e - kl * nl, j = k0 + kl, i = line0 + r;
         C a, b, c;
-        from_sigma_x(sa[sidx(T, r * 3 + 0, kl)], sa[sidx(T, r * 3 + 1, kl)], sa[sidx(T, r * 3 + 2, kl)], a, b, c);
+        const C* src = sa + r * 3 * Lp + spos(kl);
+        from_sigma_x(src[0], src[Lp], src[2 * Lp], a, b, c);
         if (!ok) continue;
         size_t o = (size_t)j * nx + i;
         A.out[o] = a;
@@ -756,13 +919,13 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     }
 }
 
-template <int MODE, typename C>
+template <int MODE, typename C, int M>
 __global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
     __shared__ double wsum[32];
-    ypass_body<MODE, C>(A, blockIdx.x, smem_raw, mbar, wsum);
+    ypass_body<MODE, C, M>(A, blockIdx.x, smem_raw, mbar, wsum);
 }
 
 template <int MODE, typename C>
@@ -774,7 +937,7 @@ __global__ void __launch_bounds__(512) ypass_batched(const PassArgsT<C>* args, c
     if ((int)blockIdx.x >= *n_items) return;
     const int2 it = items[blockIdx.x];
     const PassArgsT<C> A = args[it.x];
-    ypass_body<MODE, C>(A, it.y, smem_raw, mbar, wsum);
+    ypass_body<MODE, C, 0>(A, it.y, smem_raw, mbar, wsum);
 }
 
 // ------------------------------------------------------------- launchers ---
@@ -842,24 +1005,40 @@ static int launch_pass(K kernel, const A& a, cudaStream_t st)
     return report_cuda(cudaLaunchKernelEx(&cfg, kernel, a), "line pass cluster launch");
 }
 
+// Kernel for the tiling's chunk length: the complex64 passes have
+// register-resident solves for m = 16, 24, 32.
+template <bool X, int MODE, typename C>
+static int launch_line_pass(const PassArgsT<C>& a, cudaStream_t st)
+{
+    if constexpr (sizeof(C) == sizeof(float2)) {
+        switch (a.t.m) {
+        case 16: return X ? launch_pass(xpass_kernel<MODE, C, 16>, a, st) : launch_pass(ypass_kernel<MODE, C, 16>, a, st);
+        case 24: return X ? launch_pass(xpass_kernel<MODE, C, 24>, a, st) : launch_pass(ypass_kernel<MODE, C, 24>, a, st);
+        case 32: return X ? launch_pass(xpass_kernel<MODE, C, 32>, a, st) : launch_pass(ypass_kernel<MODE, C, 32>, a, st);
+        default: break;
+        }
+    }
+    return X ? launch_pass(xpass_kernel<MODE, C, 0>, a, st) : launch_pass(ypass_kernel<MODE, C, 0>, a, st);
+}
+
 int launch_xpass(const PassArgs& a, int mode, cudaStream_t st)
 {
-    return mode == 1 ? launch_pass(xpass_kernel<1, double2>, a, st) : launch_pass(xpass_kernel<0, double2>, a, st);
+    return mode == 1 ? launch_line_pass<true, 1>(a, st) : launch_line_pass<true, 0>(a, st);
 }
 
 int launch_ypass(const PassArgs& a, int mode, cudaStream_t st)
 {
-    return mode == 1 ? launch_pass(ypass_kernel<1, double2>, a, st) : launch_pass(ypass_kernel<0, double2>, a, st);
+    return mode == 1 ? launch_line_pass<false, 1>(a, st) : launch_line_pass<false, 0>(a, st);
 }
 
 int launch_xpass(const PassArgsF& a, int mode, cudaStream_t st)
 {
-    return mode == 1 ? launch_pass(xpass_kernel<1, float2>, a, st) : launch_pass(xpass_kernel<0, float2>, a, st);
+    return mode == 1 ? launch_line_pass<true, 1>(a, st) : launch_line_pass<true, 0>(a, st);
 }
 
 int launch_ypass(const PassArgsF& a, int mode, cudaStream_t st)
 {
-    return mode == 1 ? launch_pass(ypass_kernel<1, float2>, a, st) : launch_pass(ypass_kernel<0, float2>, a, st);
+    return mode == 1 ? launch_line_pass<false, 1>(a, st) : launch_line_pass<false, 0>(a, st);
 }
 
 // Batched launches: grid = capacity items (CTAs past *n_items exit at once),
