@@ -76,10 +76,11 @@ double max_cp(const gp_params& p, int dir, int mode)
 // per row); R lines per CTA within ~100 KB of shared memory (two CTAs per SM)
 // and 512 threads.
 // Bank conflicts of the solve's chunk-parallel shared-memory accesses: thread
-// tid = ql * nl3 + lc reads element lc * Lp + ql * cs + t, and the threads of each
-// group of G (G = 128 bytes / element size, one shared-memory wavefront) should
-// fall on distinct banks, i.e. differ modulo G.  Returns the extra wavefronts.
-static int solve_conflicts(int cs, int Lp, int nl3, int Qc, int G)
+// tid = ql * nl3 + lc accesses element lc * Lp + ql * cs + t in units of `unit`
+// elements (one access), and the threads of each group of G accesses served by
+// one 128-byte wavefront should fall on distinct banks, i.e. their offsets in
+// units differ modulo G.  Returns the extra wavefronts.
+static int solve_conflicts(int cs, int Lp, int nl3, int Qc, int G, int unit)
 {
     const int n = nl3 * Qc;
     int extra = 0;
@@ -87,36 +88,43 @@ static int solve_conflicts(int cs, int Lp, int nl3, int Qc, int G)
         int cnt[16] = {0}, mx = 0;
         for (int tid = g0; tid < std::min(n, g0 + G); ++tid) {
             const int ql = tid / nl3, lc = tid - ql * nl3;
-            mx = std::max(mx, ++cnt[(lc * Lp + ql * cs) % G]);
+            mx = std::max(mx, ++cnt[((lc * Lp + ql * cs) / unit) % G]);
         }
         extra += mx - 1;
     }
     return extra;
 }
 
-int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_req, LineTiling* t)
+int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_req, LineTiling* t)
 {
     if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
     if (S < 1 || S > 8 || (S & (S - 1)) || R < 1) return GP_ERR_ARG;  // portable cluster sizes
-    const double bits = fp32 ? 26.0 : 60.0;
-    const size_t elem = fp32 ? sizeof(float2) : sizeof(double2);
+    if (kind < TILE_C128 || kind > TILE_C64_REG) return GP_ERR_ARG;
+    const bool c64 = kind != TILE_C128;
+    const double bits = c64 ? 26.0 : 60.0;
+    const size_t elem = c64 ? sizeof(float2) : sizeof(double2);
     int F = cpmax > 0 ? (int)std::ceil(bits * std::log(2.0) / -std::log(cpmax)) + 1 : 1;
     int H = (F + 1) / 2 + 2;
     if (F > kFix || H > kHead) return GP_ERR_UNSUPPORTED;
     int m = std::max(std::max(16, H + F), m_req);
     m = (m + 3) / 4 * 4;
-    if (fp32 && m <= 32) m = m <= 16 ? 16 : (m <= 24 ? 24 : 32);  // the register-resident solves
+    if (kind == TILE_C64_REG && m <= 32) m = m <= 16 ? 16 : (m <= 24 ? 24 : 32);
+    const bool single = kind == TILE_C64_REG && m <= 32;
     int Q = (L + m - 1) / m;
     if (S > 1 && Q < 2 * S) return GP_ERR_ARG;  // at least two chunks per CTA
     const int Qc = (Q + S - 1) / S;
     if (3 * R * Qc > 512 || R > nlines) return GP_ERR_ARG;
-    // strides: fewest bank conflicts, then least shared memory
-    const int G = fp32 ? 16 : 8;
+    // strides: fewest bank conflicts, then least shared memory.  With one line
+    // array the chunks are staged in place by 16-byte bulk copies and the solve
+    // moves two complex64 per access: even strides, conflicts counted per
+    // 16-byte access (8 per wavefront).
+    const int unit = single ? 2 : 1;
+    const int G = single ? 8 : (c64 ? 16 : 8);
     int cs = m, Lp = Qc * m, best = -1;
-    for (int dc = 0; dc < G; ++dc)
-        for (int dl = 0; dl < G; ++dl) {
+    for (int dc = 0; dc < G * unit; dc += unit)
+        for (int dl = 0; dl < G * unit; dl += unit) {
             const int c = m + dc, l = Qc * c + dl;
-            const int k = solve_conflicts(c, l, 3 * R, Qc, G);
+            const int k = solve_conflicts(c, l, 3 * R, Qc, G, unit);
             if (best < 0 || k < best || (k == best && l < Lp)) {
                 best = k;
                 cs = c;
@@ -124,7 +132,8 @@ int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_r
             }
         }
     auto up = [](size_t b) { return (b + 127) / 128 * 128; };
-    const size_t smem = up(3 * R * Lp * elem) * 2 + 2 * up(3 * R * Qc * elem);
+    const size_t line_bytes = up(3 * R * Lp * elem);
+    const size_t smem = line_bytes * (single ? 1 : 2) + 2 * up(3 * R * Qc * elem);
     if (smem > 227 * 1024) return GP_ERR_UNSUPPORTED;
     t->L = L;
     t->nlines = nlines;
@@ -138,20 +147,21 @@ int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m_r
     t->Lp = Lp;
     t->threads = std::min(512, (std::max(32, 3 * R * Qc) + 31) / 32 * 32);
     t->smem = smem;
-    t->off_b = up(3 * R * Lp * elem);
-    t->off_cf = 2 * t->off_b;
+    t->off_b = single ? 0 : line_bytes;
+    t->off_cf = line_bytes * (single ? 1 : 2);
     t->off_cb = t->off_cf + up(3 * R * Qc * elem);
     t->bulk = 0;  // set per pass by the caller (needs 16-byte aligned rows)
+    t->single = single ? 1 : 0;
     return GP_OK;
 }
 
 // Default tiling: the minimum chunk length, lines per CTA within ~100 KB of
 // shared memory and 256 threads, and long lines (>= 256 points) split over a
 // 2-CTA cluster (twice the work units for the SMs, half the shared memory per CTA).
-int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32, int split)
+int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int kind, int split)
 {
     LineTiling base;
-    int st = make_tiling(L, nlines, cpmax, fp32, 1, 1, 0, &base);
+    int st = make_tiling(L, nlines, cpmax, kind, 1, 1, 0, &base);
     if (st) return st;
     int m = base.m, Q = base.Q;
     while (3 * Q > 512) {  // keep one thread per chunk within a CTA
@@ -161,11 +171,11 @@ int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32, int 
     const int S = (split && L >= 256 && Q >= 8) ? 2 : 1;
     const int Qc = (Q + S - 1) / S;
     int R = std::max(1, 256 / (3 * Qc));
-    if (fp32 && S == 1) R = std::max(R, 4);  // >= 32-byte segments in the transposed store
+    if (kind != TILE_C128 && S == 1) R = std::max(R, 4);  // >= 32-byte segments in the transposed store
     if (S > 1) R = 1;
     R = std::min(R, nlines);
     for (; R >= 1; --R) {
-        if (make_tiling(L, nlines, cpmax, fp32, S, R, m, t) == GP_OK && (R == 1 || t->smem <= 100 * 1024)) return GP_OK;
+        if (make_tiling(L, nlines, cpmax, kind, S, R, m, t) == GP_OK && (R == 1 || t->smem <= 100 * 1024)) return GP_OK;
     }
     return GP_ERR_UNSUPPORTED;
 }
@@ -221,13 +231,13 @@ int ensure_coef(gp_handle* h, int mode)
     int st = choose_tiling(p.nx, p.ny, cx, &tx);
     if (st) return st;
     if ((st = choose_tiling(p.ny, p.nx, cy, &ty))) return st;
-    if ((st = choose_tiling(p.nx, p.ny, cx, &ux, 0, 0))) return st;
-    if ((st = choose_tiling(p.ny, p.nx, cy, &uy, 0, 0))) return st;
+    if ((st = choose_tiling(p.nx, p.ny, cx, &ux, TILE_C128, 0))) return st;
+    if ((st = choose_tiling(p.ny, p.nx, cy, &uy, TILE_C128, 0))) return st;
     if (f32) {
-        if ((st = choose_tiling(p.nx, p.ny, cx, &ftx, 1))) return st;
-        if ((st = choose_tiling(p.ny, p.nx, cy, &fty, 1))) return st;
-        if ((st = choose_tiling(p.nx, p.ny, cx, &fux, 1, 0))) return st;
-        if ((st = choose_tiling(p.ny, p.nx, cy, &fuy, 1, 0))) return st;
+        if ((st = choose_tiling(p.nx, p.ny, cx, &ftx, TILE_C64_REG))) return st;
+        if ((st = choose_tiling(p.ny, p.nx, cy, &fty, TILE_C64_REG))) return st;
+        if ((st = choose_tiling(p.nx, p.ny, cx, &fux, TILE_C64, 0))) return st;  // batched launches
+        if ((st = choose_tiling(p.ny, p.nx, cy, &fuy, TILE_C64, 0))) return st;
     }
     if (!cs.cx) {
         bool ok = cudaMalloc(&cs.cx, sizeof(LineCoef) * 3 * (size_t)p.ny) == cudaSuccess &&
@@ -793,10 +803,12 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
         float best_ms = -1.0f;
         const int ms_add[] = {0, 4, 8, 16, 32};
         for (int S : {1, 2, 4, 8})
-            for (int R : {1, 2, 4})
+            for (int R : {1, 2, 4, 8})
                 for (int add : ms_add) {
                     LineTiling t;
-                    if (make_tiling(L, nl, cp, f32, S, R, cur.m - (cur.m % 4) + add, &t) != GP_OK) continue;
+                    if (make_tiling(L, nl, cp, f32 ? TILE_C64_REG : TILE_C128, S, R, cur.m - (cur.m % 4) + add, &t) !=
+                        GP_OK)
+                        continue;
                     if (S > 1 && L < 64) continue;
                     float ms;
                     if (f32) {
@@ -838,8 +850,8 @@ int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_ct
     const gp_params& p = h->p;
     const bool f32 = h->active == GP_FP32_MIXED;
     LineTiling t;
-    st = make_tiling(dir == 0 ? p.nx : p.ny, dir == 0 ? p.ny : p.nx, max_cp(p, dir, mode), f32, cluster,
-                     lines_per_cta, chunk, &t);
+    st = make_tiling(dir == 0 ? p.nx : p.ny, dir == 0 ? p.ny : p.nx, max_cp(p, dir, mode),
+                     f32 ? TILE_C64_REG : TILE_C128, cluster, lines_per_cta, chunk, &t);
     if (st) return st;
     (f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty)) = t;
     drop_graphs(h);

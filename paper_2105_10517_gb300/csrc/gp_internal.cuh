@@ -72,7 +72,12 @@ struct LineTiling {
     size_t off_cf; // staging area of the bulk row copies) and of the carry arrays
     size_t off_cb;
     int bulk;      // rows are 16-byte aligned: stage them with cp.async.bulk
+    int single;    // one line array: rows are staged in place (complex64 register-resident solve, m = 16/24/32)
 };
+
+// Kinds of tiling: complex128; complex64 with the shared-memory solve (two line
+// arrays, any chunk length); complex64 with the register-resident solve.
+enum TileKind { TILE_C128 = 0, TILE_C64 = 1, TILE_C64_REG = 2 };
 
 template <typename C>
 struct PassArgsT {
@@ -105,10 +110,10 @@ double gamma_of(const gp_params& p);
 double max_cp(const gp_params& p, int dir, int mode);
 // fp32 = 1: tiling for complex64 lines (fixups to 2^-26 instead of 2^-60)
 // split = 1 allows a line group to span a 2-CTA cluster (not for batched launches).
-int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int fp32 = 0, int split = 1);
+int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int kind = TILE_C128, int split = 1);
 // A specific tiling (autotuner candidates): S CTAs per line group, R lines per
 // CTA, chunk length m (raised to the minimum the precision needs).
-int make_tiling(int L, int nlines, double cpmax, int fp32, int S, int R, int m, LineTiling* t);
+int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m, LineTiling* t);
 
 // launchers (gp_sweeps.cu)
 int launch_coef(LineCoef* coef, int nlines, int dir, int mode, double h, double line_len, double line_h,

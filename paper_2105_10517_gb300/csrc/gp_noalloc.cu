@@ -106,8 +106,8 @@ extern "C" int gp_propagate_noalloc(const gp_params* params, double* psi_dev, lo
     // unsplit tilings: one CTA per line group, so the y-pass writes at most
     // kMaxLine partial norms into g_partials
     LineTiling tx, ty;
-    if ((st = choose_tiling(p.nx, p.ny, max_cp(p, 0, mode), &tx, 0, 0))) return st;
-    if ((st = choose_tiling(p.ny, p.nx, max_cp(p, 1, mode), &ty, 0, 0))) return st;
+    if ((st = choose_tiling(p.nx, p.ny, max_cp(p, 0, mode), &tx, TILE_C128, 0))) return st;
+    if ((st = choose_tiling(p.ny, p.nx, max_cp(p, 1, mode), &ty, TILE_C128, 0))) return st;
     if ((ty.nlines + ty.R - 1) / ty.R * ty.S > kMaxLine) return GP_ERR_TOO_LARGE;
 
     // The arrays keep the previous call's contents: the flag must start at zero

@@ -110,11 +110,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err)
 }
 
 // Stages row segments base + c * plane + (line0 + r) * L + k0 .. + len for
-// r < nl, c < 3 into dst[(r * 3 + c) * len].  Segments must be 16-byte aligned
-// and a multiple of 16 bytes long.
+// r < nl, c < 3 into dst[(r * 3 + c) * stride].  Segments and destination rows
+// must be 16-byte aligned and a multiple of 16 bytes long.
 template <typename C>
 __device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, int line0, int nl, int L, int k0,
-                                           int len, uint64_t* mbar, int* err)
+                                           int len, int stride, uint64_t* mbar, int* err)
 {
     if (threadIdx.x == 0) mbar_init(mbar, 1);
     __syncthreads();
@@ -123,8 +123,31 @@ __device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, 
         mbar_expect_tx(mbar, seg_bytes * 3u * (uint32_t)nl);
         for (int r = 0; r < nl; ++r)
             for (int c = 0; c < 3; ++c)
-                bulk_g2s(dst + (size_t)(r * 3 + c) * len, base + c * plane + (size_t)(line0 + r) * L + k0, seg_bytes,
+                bulk_g2s(dst + (size_t)(r * 3 + c) * stride, base + c * plane + (size_t)(line0 + r) * L + k0, seg_bytes,
                          mbar);
+    }
+    return mbar_wait_bounded(mbar, err);
+}
+
+// One-array layout: stages the chunks of the CTA's line segments, one bulk copy
+// per chunk issued by the thread that solves it (u = ql * 3 nl + lc), chunk
+// (lc, ql) of line point k0 + ql m .. to dst[lc * Lp + ql * cs].  Rows must be
+// 16-byte aligned (even L); m, cs and Lp are even.
+template <typename C>
+__device__ __forceinline__ bool stage_chunks(C* dst, const C* base, size_t plane, int line0, int nl, int L, int k0,
+                                             int len, int m, int cs, int Lp, uint64_t* mbar, int* err)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        mbar_expect_tx(mbar, (uint32_t)(3 * nl * len * sizeof(C)));
+    }
+    __syncthreads();
+    const int nl3 = 3 * nl, nq = (len + m - 1) / m;
+    for (int u = threadIdx.x; u < nl3 * nq; u += blockDim.x) {
+        const int ql = u / nl3, lc = u - ql * nl3, r = lc / 3, c = lc - 3 * r;
+        const int k = ql * m, n = min(m, len - k);
+        bulk_g2s(dst + lc * Lp + ql * cs, base + c * plane + (size_t)(line0 + r) * L + k0 + k,
+                 (uint32_t)(n * sizeof(C)), mbar);
     }
     return mbar_wait_bounded(mbar, err);
 }
@@ -550,6 +573,21 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
     group_sync(T);
 }
 
+// Converged factorisation of the thread's line-channel (chunk-major mapping:
+// lc = tid mod 3 nl), loaded at the start of a pass so that the global-memory
+// latency overlaps the staging and pointwise work.
+template <typename C>
+struct ConvCoef {
+    C inv, g, cp;
+};
+
+template <typename C>
+__device__ __forceinline__ ConvCoef<C> load_conv(const LineCoefT<C>* coef, const Part& P)
+{
+    const LineCoefT<C>* Co = coef + (int)(threadIdx.x % (unsigned)(3 * max(P.nl, 1)));
+    return ConvCoef<C>{Co->inv[kHead - 1], Co->g[kHead - 1], Co->cp[kHead - 1]};
+}
+
 // The same solve with the chunk length M fixed at compile time and each
 // thread's chunk of y / w held in registers: shared memory is read for phi in
 // the forward sweep and in the final step and written once with psi'.
@@ -558,9 +596,10 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
 // they use the converged coefficients throughout; chunk 0 takes the table rows.
 template <typename C, int M>
 __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const LineCoefT<C>* coef,
-                                                   const LineTiling& T, const Part& P)
+                                                   const ConvCoef<C>& cc, const LineTiling& T, const Part& P)
 {
     typedef typename RealOf<C>::type R;
+    static_assert(sizeof(C) == 8 && M % 2 == 0, "pairs of complex64 per 16-byte shared-memory access");
     const int Q = T.Q, F = T.F, L = T.L, Lp = T.Lp, Qc = T.Qc;
     const int nl3 = 3 * max(P.nl, 1);
     const int tid = threadIdx.x;
@@ -579,23 +618,31 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
         if (P.rank < T.S - 1) cb_next = cl.map_shared_rank(cb, P.rank + 1);
     }
     const C zero = mkc<C>(R(0), R(0));
-    const C inv_c = Co->inv[kHead - 1], g_c = Co->g[kHead - 1], cp_c = Co->cp[kHead - 1];
+    const C inv_c = cc.inv, g_c = cc.g, cp_c = cc.cp;
     C y[M];
     if (active) {
         // forward elimination from a zero carry; rows past the line end stay zero
         C v = zero;
+        // phi two points per 16-byte load (chunk starts are 16-byte aligned)
+        const float4* p4 = reinterpret_cast<const float4*>(pa);
         if (q == 0) {
 #pragma unroll
-            for (int t = 0; t < M; ++t) {
-                const int k = t < kHead - 1 ? t : kHead - 1;
-                v = cfnma(Co->g[k], v, cmul(Co->inv[k], pa[t]));
+            for (int t = 0; t < M; t += 2) {
+                const float4 d = p4[t / 2];
+                const int k0 = t < kHead - 1 ? t : kHead - 1, k1 = t + 1 < kHead - 1 ? t + 1 : kHead - 1;
+                v = cfnma(Co->g[k0], v, cmul(Co->inv[k0], mkc<C>(d.x, d.y)));
                 y[t] = t < len ? v : zero;
+                v = cfnma(Co->g[k1], v, cmul(Co->inv[k1], mkc<C>(d.z, d.w)));
+                y[t + 1] = t + 1 < len ? v : zero;
             }
         } else {
 #pragma unroll
-            for (int t = 0; t < M; ++t) {
-                v = cfnma(g_c, v, cmul(inv_c, pa[t]));
+            for (int t = 0; t < M; t += 2) {
+                const float4 d = p4[t / 2];
+                v = cfnma(g_c, v, cmul(inv_c, mkc<C>(d.x, d.y)));
                 y[t] = t < len ? v : zero;
+                v = cfnma(g_c, v, cmul(inv_c, mkc<C>(d.z, d.w)));
+                y[t + 1] = t + 1 < len ? v : zero;
             }
         }
         cf[lc * Qc + ql] = y[M - 1];
@@ -659,11 +706,14 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
                     if (t >= M - F) y[t] = cfma(Co->pb[M - 1 - t], wc, y[t]);
             }
         }
+        // psi' = 2 w - phi, two points per 16-byte access (len is even)
 #pragma unroll
-        for (int t = 0; t < M; ++t) {
+        for (int t = 0; t < M; t += 2) {
             if (t < len) {
-                const C ph = pa[t];
-                pa[t] = mkc<C>(fma(R(2), y[t].x, -ph.x), fma(R(2), y[t].y, -ph.y));
+                float4* p4 = reinterpret_cast<float4*>(pa) + t / 2;
+                const float4 d = *p4;
+                *p4 = make_float4(fma(R(2), y[t].x, -d.x), fma(R(2), y[t].y, -d.y), fma(R(2), y[t + 1].x, -d.z),
+                                  fma(R(2), y[t + 1].y, -d.w));
             }
         }
     }
@@ -675,10 +725,10 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
 // compiled for the tiling's chunk length M, the shared-memory form for M = 0.
 template <typename C, int M>
 __device__ __forceinline__ void solve_lines(C* sa, C* sb, C* cf, C* cb, const LineCoefT<C>* coef,
-                                            const LineTiling& T, const Part& P)
+                                            const ConvCoef<C>& cc, const LineTiling& T, const Part& P)
 {
     if constexpr (M > 0)
-        chunked_thomas_reg<C, M>(sa, cf, cb, coef, T, P);
+        chunked_thomas_reg<C, M>(sa, cf, cb, coef, cc, T, P);
     else
         chunked_thomas(sa, sb, cf, cb, coef, T, P);
 }
@@ -722,7 +772,16 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     // stage the CTA's row segments psi[c][j][k0 .. k0 + Ll) into sb ([r][c][k] contiguous).
     // If the bounded wait gives up (status bit set), the CTA still runs every
     // barrier -- the other CTA of its cluster waits on them -- but writes nothing.
-    const bool ok = !(T.bulk && Ll > 0) || stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, &mbar, A.err);
+    ConvCoef<C> cc{};
+    if (M > 0 && A.do_solve) cc = load_conv(A.coef + (size_t)line0 * 3, P);
+    // with one line array (M > 0) the chunks are staged in place
+    bool ok = true;
+    if (T.bulk && Ll > 0) {
+        if constexpr (M > 0)
+            ok = stage_chunks(sa, A.in, plane, line0, nl, L, k0, Ll, T.m, T.cs, T.Lp, &mbar, A.err);
+        else
+            ok = stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, Ll, &mbar, A.err);
+    }
 
     // Per-CTA constants, computed once by thread 0 (FP64 work is costly on this
     // part even inside the complex64 pass) and broadcast through shared memory.
@@ -755,10 +814,11 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         int r = div_len(e), kl = e - r * Ll, i = k0 + kl, j = line0 + r;
         C a, b, c;
         if (T.bulk) {
-            const C* row = sb + (size_t)r * 3 * Ll + kl;
+            const int ss = M > 0 ? Lp : Ll;
+            const C* row = M > 0 ? sa + r * 3 * Lp + spos(kl) : sb + (size_t)r * 3 * Ll + kl;
             a = row[0];
-            b = row[Ll];
-            c = row[2 * Ll];
+            b = row[ss];
+            c = row[2 * ss];
         } else {
             size_t o = (size_t)j * nx + i;
             a = A.in[o];
@@ -789,7 +849,7 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         dst[2 * Lp] = m;
     }
     __syncthreads();
-    if (A.do_solve) solve_lines<C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, P);
+    if (A.do_solve) solve_lines<C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P);
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, i = k0 + kl, j = line0 + r;
@@ -804,9 +864,21 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     }
 }
 
-// M: chunk length of a register-resident solve, 0 for the shared-memory solve
-template <int MODE, typename C, int M>
+// Single-instance passes with the shared-memory solve.
+template <int MODE, typename C>
 __global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    xpass_body<MODE, C, 0>(A, blockIdx.x, smem_raw, mbar);
+}
+
+// With the register-resident solve of chunk length M (one-array tilings).  The
+// register caps (a few dozen bytes of spill at most) keep five to ten CTAs per SM.
+constexpr int reg_cap(int M) { return M == 16 ? 64 : (M == 24 ? 80 : 96); }
+
+template <int MODE, typename C, int M>
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) xpass_kernel_reg(PassArgsT<C> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
@@ -845,12 +917,22 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     const size_t plane = (size_t)nx * ny;
     // stage the CTA's row segments t[mu][i][k0 .. k0 + Ll) into sb ([r][mu][k] contiguous);
     // on a timeout the CTA runs every barrier but writes nothing (see the x-pass)
-    const bool ok = !(T.bulk && Ll > 0) || stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, &mbar, A.err);
+    ConvCoef<C> cc{};
+    if (M > 0 && A.do_solve) cc = load_conv(A.coef + (size_t)line0 * 3, P);
+    // with one line array (M > 0) the chunks are staged in place and need no copy
+    bool ok = true;
+    if (T.bulk && Ll > 0) {
+        if constexpr (M > 0)
+            ok = stage_chunks(sa, A.in, plane, line0, nl, L, k0, Ll, T.m, T.cs, T.Lp, &mbar, A.err);
+        else
+            ok = stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, Ll, &mbar, A.err);
+    }
 
     const FastDiv div_len(Ll), div_nl(nl);
     const SPos spos(T);
     const int Lp = T.Lp;
-    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+    const bool copy_in = !(M > 0 && T.bulk);
+    for (int e = threadIdx.x; copy_in && threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int r = div_len(e), kl = e - r * Ll, j = k0 + kl, i = line0 + r;
         C* dst = sa + r * 3 * Lp + spos(kl);
         if (T.bulk) {
@@ -866,7 +948,7 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
         }
     }
     __syncthreads();
-    if (A.do_solve) solve_lines<C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, T, P);
+    if (A.do_solve) solve_lines<C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P);
     R acc = R(0), acc3[3] = {R(0), R(0), R(0)};
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, j = k0 + kl, i = line0 + r;
@@ -919,8 +1001,17 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     }
 }
 
-template <int MODE, typename C, int M>
+template <int MODE, typename C>
 __global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    __shared__ double wsum[32];
+    ypass_body<MODE, C, 0>(A, blockIdx.x, smem_raw, mbar, wsum);
+}
+
+template <int MODE, typename C, int M>
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) ypass_kernel_reg(PassArgsT<C> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
@@ -1005,20 +1096,24 @@ static int launch_pass(K kernel, const A& a, cudaStream_t st)
     return report_cuda(cudaLaunchKernelEx(&cfg, kernel, a), "line pass cluster launch");
 }
 
-// Kernel for the tiling's chunk length: the complex64 passes have
-// register-resident solves for m = 16, 24, 32.
+// Kernel for the tiling: a one-array complex64 tiling (m = 16, 24, 32) runs the
+// register-resident solve compiled for its m, every other tiling the
+// shared-memory solve.
 template <bool X, int MODE, typename C>
 static int launch_line_pass(const PassArgsT<C>& a, cudaStream_t st)
 {
-    if constexpr (sizeof(C) == sizeof(float2)) {
-        switch (a.t.m) {
-        case 16: return X ? launch_pass(xpass_kernel<MODE, C, 16>, a, st) : launch_pass(ypass_kernel<MODE, C, 16>, a, st);
-        case 24: return X ? launch_pass(xpass_kernel<MODE, C, 24>, a, st) : launch_pass(ypass_kernel<MODE, C, 24>, a, st);
-        case 32: return X ? launch_pass(xpass_kernel<MODE, C, 32>, a, st) : launch_pass(ypass_kernel<MODE, C, 32>, a, st);
-        default: break;
+    if (a.t.single) {
+        if constexpr (sizeof(C) == sizeof(float2)) {
+            switch (a.t.m) {
+            case 16: return X ? launch_pass(xpass_kernel_reg<MODE, C, 16>, a, st) : launch_pass(ypass_kernel_reg<MODE, C, 16>, a, st);
+            case 24: return X ? launch_pass(xpass_kernel_reg<MODE, C, 24>, a, st) : launch_pass(ypass_kernel_reg<MODE, C, 24>, a, st);
+            case 32: return X ? launch_pass(xpass_kernel_reg<MODE, C, 32>, a, st) : launch_pass(ypass_kernel_reg<MODE, C, 32>, a, st);
+            default: break;
+            }
         }
+        return GP_ERR_ARG;  // one line array only with a register-resident solve
     }
-    return X ? launch_pass(xpass_kernel<MODE, C, 0>, a, st) : launch_pass(ypass_kernel<MODE, C, 0>, a, st);
+    return X ? launch_pass(xpass_kernel<MODE, C>, a, st) : launch_pass(ypass_kernel<MODE, C>, a, st);
 }
 
 int launch_xpass(const PassArgs& a, int mode, cudaStream_t st)
