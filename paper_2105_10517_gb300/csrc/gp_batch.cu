@@ -57,32 +57,65 @@ struct Request {
     std::vector<double> psi;  // result, complex128, after completion
 };
 
+// Work items of one pass whose tilings share a solve kind: the shared-memory
+// solve (class 0) or the register-resident solve of chunk length 16, 24, 32.
+constexpr int kSolveClasses = 4;
+constexpr int kClassM[kSolveClasses] = {0, 16, 24, 32};
+
+int solve_class(const LineTiling& t)
+{
+    if (!t.single) return 0;
+    return t.m == 16 ? 1 : (t.m == 24 ? 2 : 3);
+}
+
+struct PassList {
+    std::vector<int2> items;
+    int threads = 0;
+    size_t smem = 0;
+    DevBuf<int2> d;
+    void clear()
+    {
+        items.clear();
+        threads = 0;
+        smem = 0;
+    }
+    void add(int inst, const LineTiling& t)
+    {
+        const int n = y_blocks(t);
+        for (int c = 0; c < n; ++c) items.push_back(make_int2(inst, c));
+        threads = std::max(threads, t.threads);
+        smem = std::max(smem, t.smem);
+    }
+};
+
+// Counts (device) per group: work items of the x and y classes, then instances.
+constexpr int kGroupCounts = 2 * kSolveClasses + 1;
+
 template <typename C>
 struct Group {
     std::vector<PassArgsT<C>> ax, ay;
-    std::vector<int2> ix, iy;
+    PassList lx[kSolveClasses], ly[kSolveClasses];
     std::vector<FinArgs> fin;
-    int tx = 0, ty = 0;
-    size_t sx = 0, sy = 0;
     DevBuf<PassArgsT<C>> dax, day;
-    DevBuf<int2> dix, diy;
     DevBuf<FinArgs> dfin;
     void clear()
     {
         ax.clear();
         ay.clear();
-        ix.clear();
-        iy.clear();
+        for (int c = 0; c < kSolveClasses; ++c) {
+            lx[c].clear();
+            ly[c].clear();
+        }
         fin.clear();
-        tx = ty = 0;
-        sx = sy = 0;
     }
     void release()
     {
         dax.release();
         day.release();
-        dix.release();
-        diy.release();
+        for (int c = 0; c < kSolveClasses; ++c) {
+            lx[c].d.release();
+            ly[c].d.release();
+        }
         dfin.release();
     }
 };
@@ -99,7 +132,7 @@ struct gp_batch {
     std::map<long long, Request> reqs;
     Group<double2> g64;
     Group<float2> g32;
-    int* counts = nullptr;  // device: [n_x64, n_y64, n_inst64, n_x32, n_y32, n_inst32]
+    int* counts = nullptr;  // device: kGroupCounts per precision group (complex128, complex64)
     int* flag = nullptr;
 };
 
@@ -126,14 +159,9 @@ void add_instance(Group<C>& g, gp_handle* h, const PassArgsT<C>& ax, PassArgsT<C
     ay.partials = h->partials;
     g.ax.push_back(ax);
     g.ay.push_back(ay);
-    const int cx = y_blocks(ax.t), cy = y_blocks(ay.t);
-    for (int c = 0; c < cx; ++c) g.ix.push_back(make_int2(inst, c));
-    for (int c = 0; c < cy; ++c) g.iy.push_back(make_int2(inst, c));
-    g.fin.push_back(FinArgs{h->partials, cy, cell(h), h->scal});
-    g.tx = std::max(g.tx, ax.t.threads);
-    g.ty = std::max(g.ty, ay.t.threads);
-    g.sx = std::max(g.sx, ax.t.smem);
-    g.sy = std::max(g.sy, ay.t.smem);
+    g.lx[solve_class(ax.t)].add(inst, ax.t);
+    g.ly[solve_class(ay.t)].add(inst, ay.t);
+    g.fin.push_back(FinArgs{h->partials, y_blocks(ay.t), cell(h), h->scal});
 }
 
 template <typename C>
@@ -141,21 +169,41 @@ int upload_and_run(gp_batch* b, Group<C>& g, int* counts, int steps)
 {
     if (g.ax.empty()) return GP_OK;
     int st;
-    if ((st = g.dax.reserve(g.ax.size())) || (st = g.day.reserve(g.ay.size())) || (st = g.dix.reserve(g.ix.size())) ||
-        (st = g.diy.reserve(g.iy.size())) || (st = g.dfin.reserve(g.fin.size())))
+    if ((st = g.dax.reserve(g.ax.size())) || (st = g.day.reserve(g.ay.size())) || (st = g.dfin.reserve(g.fin.size())))
         return st;
     cudaStream_t s = b->stream;
+    int n[kGroupCounts];
+    for (int c = 0; c < kSolveClasses; ++c) {
+        PassList* lists[2] = {&g.lx[c], &g.ly[c]};
+        for (int d = 0; d < 2; ++d) {
+            PassList& l = *lists[d];
+            n[d * kSolveClasses + c] = (int)l.items.size();
+            if (l.items.empty()) continue;
+            if ((st = l.d.reserve(l.items.size()))) return st;
+            BK(cudaMemcpyAsync(l.d.p, l.items.data(), l.items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        }
+    }
+    n[2 * kSolveClasses] = (int)g.fin.size();
     BK(cudaMemcpyAsync(g.dax.p, g.ax.data(), g.ax.size() * sizeof(g.ax[0]), cudaMemcpyHostToDevice, s));
     BK(cudaMemcpyAsync(g.day.p, g.ay.data(), g.ay.size() * sizeof(g.ay[0]), cudaMemcpyHostToDevice, s));
-    BK(cudaMemcpyAsync(g.dix.p, g.ix.data(), g.ix.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-    BK(cudaMemcpyAsync(g.diy.p, g.iy.data(), g.iy.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     BK(cudaMemcpyAsync(g.dfin.p, g.fin.data(), g.fin.size() * sizeof(FinArgs), cudaMemcpyHostToDevice, s));
-    const int n[3] = {(int)g.ix.size(), (int)g.iy.size(), (int)g.fin.size()};
     BK(cudaMemcpyAsync(counts, n, sizeof(n), cudaMemcpyHostToDevice, s));
     for (int k = 0; k < steps; ++k) {
-        if (launch_xpass_batched(g.dax.p, g.dix.p, counts, n[0], g.tx, g.sx, GP_IMAG, s)) return GP_ERR_CUDA;
-        if (launch_ypass_batched(g.day.p, g.diy.p, counts + 1, n[1], g.ty, g.sy, GP_IMAG, s)) return GP_ERR_CUDA;
-        if (launch_finalize_norm_batched(g.dfin.p, counts + 2, n[2], b->flag, s)) return GP_ERR_CUDA;
+        for (int c = 0; c < kSolveClasses; ++c) {
+            const PassList& l = g.lx[c];
+            if (!l.items.empty() && launch_xpass_batched(g.dax.p, l.d.p, counts + c, (int)l.items.size(), l.threads,
+                                                         l.smem, GP_IMAG, s, kClassM[c]))
+                return GP_ERR_CUDA;
+        }
+        for (int c = 0; c < kSolveClasses; ++c) {
+            const PassList& l = g.ly[c];
+            if (!l.items.empty() && launch_ypass_batched(g.day.p, l.d.p, counts + kSolveClasses + c,
+                                                         (int)l.items.size(), l.threads, l.smem, GP_IMAG, s,
+                                                         kClassM[c]))
+                return GP_ERR_CUDA;
+        }
+        if (launch_finalize_norm_batched(g.dfin.p, counts + 2 * kSolveClasses, n[2 * kSolveClasses], b->flag, s))
+            return GP_ERR_CUDA;
     }
     return GP_OK;
 }
@@ -235,7 +283,7 @@ int gp_batch_create(size_t max_device_bytes, int check_every, void* cuda_stream,
         }
         b->own_stream = true;
     }
-    if (cudaMalloc(&b->counts, 8 * sizeof(int)) != cudaSuccess || cudaMalloc(&b->flag, sizeof(int)) != cudaSuccess ||
+    if (cudaMalloc(&b->counts, 2 * kGroupCounts * sizeof(int)) != cudaSuccess || cudaMalloc(&b->flag, sizeof(int)) != cudaSuccess ||
         cudaMemsetAsync(b->flag, 0, sizeof(int), b->stream) != cudaSuccess) {
         gp_batch_destroy(b);
         return GP_ERR_OOM;
@@ -307,7 +355,7 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
     const int k = b->check_every;
     if (!run.empty()) {
         if ((st = upload_and_run(b, b->g64, b->counts, k))) return st;
-        if ((st = upload_and_run(b, b->g32, b->counts + 4, k))) return st;
+        if ((st = upload_and_run(b, b->g32, b->counts + kGroupCounts, k))) return st;
         BK(cudaStreamSynchronize(b->stream));
     }
     // convergence checks between ticks

@@ -236,8 +236,8 @@ int ensure_coef(gp_handle* h, int mode)
     if (f32) {
         if ((st = choose_tiling(p.nx, p.ny, cx, &ftx, TILE_C64_REG))) return st;
         if ((st = choose_tiling(p.ny, p.nx, cy, &fty, TILE_C64_REG))) return st;
-        if ((st = choose_tiling(p.nx, p.ny, cx, &fux, TILE_C64, 0))) return st;  // batched launches
-        if ((st = choose_tiling(p.ny, p.nx, cy, &fuy, TILE_C64, 0))) return st;
+        if ((st = choose_tiling(p.nx, p.ny, cx, &fux, TILE_C64_REG, 0))) return st;  // batched launches
+        if ((st = choose_tiling(p.ny, p.nx, cy, &fuy, TILE_C64_REG, 0))) return st;
     }
     if (!cs.cx) {
         bool ok = cudaMalloc(&cs.cx, sizeof(LineCoef) * 3 * (size_t)p.ny) == cudaSuccess &&

@@ -126,14 +126,17 @@ int launch_xpass(const PassArgs& a, int mode, cudaStream_t st);
 int launch_ypass(const PassArgs& a, int mode, cudaStream_t st);
 int launch_xpass(const PassArgsF& a, int mode, cudaStream_t st);
 int launch_ypass(const PassArgsF& a, int mode, cudaStream_t st);
+// Batched passes over (instance, CTA) work items; m_reg = 16/24/32 selects the
+// register-resident solve (every item's tiling one-array with that m), 0 the
+// shared-memory solve.
 int launch_xpass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st);
+                         size_t smem, int mode, cudaStream_t st, int m_reg = 0);
 int launch_ypass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st);
+                         size_t smem, int mode, cudaStream_t st, int m_reg = 0);
 int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st);
+                         size_t smem, int mode, cudaStream_t st, int m_reg = 0);
 int launch_ypass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st);
+                         size_t smem, int mode, cudaStream_t st, int m_reg = 0);
 // launchers (gp_reduce.cu)
 int launch_norm(const double2* psi, size_t n, double* partials, int nblk, double da, double* scale, int* flag,
                 cudaStream_t st);

@@ -898,6 +898,20 @@ __global__ void __launch_bounds__(512) xpass_batched(const PassArgsT<C>* args, c
     xpass_body<MODE, C, 0>(A, it.y, smem_raw, mbar);
 }
 
+// The same with the register-resident solve: every item's tiling is a one-array
+// tiling of chunk length M.
+template <int MODE, typename C, int M>
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
+    xpass_batched_reg(const PassArgsT<C>* args, const int2* items, const int* n_items)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    if ((int)blockIdx.x >= *n_items) return;
+    const int2 it = items[blockIdx.x];
+    const PassArgsT<C> A = args[it.x];
+    xpass_body<MODE, C, M>(A, it.y, smem_raw, mbar);
+}
+
 // --------------------------------------------------------------- y-pass ----
 // Partial norms: each thread sums its sites' |psi|^2 in the pass's precision
 // (a few dozen sites), the CTA then adds the threads' sums in FP64.
@@ -1031,6 +1045,19 @@ __global__ void __launch_bounds__(512) ypass_batched(const PassArgsT<C>* args, c
     ypass_body<MODE, C, 0>(A, it.y, smem_raw, mbar, wsum);
 }
 
+template <int MODE, typename C, int M>
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
+    ypass_batched_reg(const PassArgsT<C>* args, const int2* items, const int* n_items)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    __shared__ double wsum[32];
+    if ((int)blockIdx.x >= *n_items) return;
+    const int2 it = items[blockIdx.x];
+    const PassArgsT<C> A = args[it.x];
+    ypass_body<MODE, C, M>(A, it.y, smem_raw, mbar, wsum);
+}
+
 // ------------------------------------------------------------- launchers ---
 template <typename C>
 static int launch_coef_t(LineCoefT<C>* coef, int nlines, int dir, int mode, double h, double line_len,
@@ -1152,31 +1179,52 @@ static int launch_batched_t(K kernel, const PassArgsT<C>* args, const int2* item
 }
 
 int launch_xpass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st)
+                         size_t smem, int mode, cudaStream_t st, int m_reg)
 {
+    if (m_reg) return GP_ERR_ARG;  // complex128 tilings use the shared-memory solve
     return mode == 1 ? launch_batched_t(xpass_batched<1, double2>, args, items, n_items, capacity, threads, smem, st)
                      : launch_batched_t(xpass_batched<0, double2>, args, items, n_items, capacity, threads, smem, st);
 }
 
 int launch_ypass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st)
+                         size_t smem, int mode, cudaStream_t st, int m_reg)
 {
+    if (m_reg) return GP_ERR_ARG;
     return mode == 1 ? launch_batched_t(ypass_batched<1, double2>, args, items, n_items, capacity, threads, smem, st)
                      : launch_batched_t(ypass_batched<0, double2>, args, items, n_items, capacity, threads, smem, st);
 }
 
-int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st)
+template <bool X, int MODE>
+static int launch_batched_f32(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
+                              size_t smem, cudaStream_t st, int m_reg)
 {
-    return mode == 1 ? launch_batched_t(xpass_batched<1, float2>, args, items, n_items, capacity, threads, smem, st)
-                     : launch_batched_t(xpass_batched<0, float2>, args, items, n_items, capacity, threads, smem, st);
+#define GP_BATCHED(M)                                                                                              \
+    (X ? launch_batched_t(xpass_batched_reg<MODE, float2, M>, args, items, n_items, capacity, threads, smem, st) \
+       : launch_batched_t(ypass_batched_reg<MODE, float2, M>, args, items, n_items, capacity, threads, smem, st))
+    switch (m_reg) {
+    case 0:
+        return X ? launch_batched_t(xpass_batched<MODE, float2>, args, items, n_items, capacity, threads, smem, st)
+                 : launch_batched_t(ypass_batched<MODE, float2>, args, items, n_items, capacity, threads, smem, st);
+    case 16: return GP_BATCHED(16);
+    case 24: return GP_BATCHED(24);
+    case 32: return GP_BATCHED(32);
+    default: return GP_ERR_ARG;
+    }
+#undef GP_BATCHED
+}
+
+int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st, int m_reg)
+{
+    return mode == 1 ? launch_batched_f32<true, 1>(args, items, n_items, capacity, threads, smem, st, m_reg)
+                     : launch_batched_f32<true, 0>(args, items, n_items, capacity, threads, smem, st, m_reg);
 }
 
 int launch_ypass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st)
+                         size_t smem, int mode, cudaStream_t st, int m_reg)
 {
-    return mode == 1 ? launch_batched_t(ypass_batched<1, float2>, args, items, n_items, capacity, threads, smem, st)
-                     : launch_batched_t(ypass_batched<0, float2>, args, items, n_items, capacity, threads, smem, st);
+    return mode == 1 ? launch_batched_f32<false, 1>(args, items, n_items, capacity, threads, smem, st, m_reg)
+                     : launch_batched_f32<false, 0>(args, items, n_items, capacity, threads, smem, st, m_reg);
 }
 
 }  // namespace gpspin
