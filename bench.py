@@ -269,7 +269,9 @@ def run_ours(args):
 
     dom = "xpass" if ms_x >= ms_y else "ypass"
     ms_dom = ms_x if dom == "xpass" else ms_y
-    kname = f"{dom}_kernel<{mode}, {'float2' if prec == 'fp32' else 'double2'}>"
+    td = tiles[dom]
+    kname = (f"{dom}_kernel_reg<{mode}, float2, {td['chunk']}>" if td.get("register_solve")
+             else f"{dom}_kernel<{mode}, {'float2' if prec == 'fp32' else 'double2'}>")
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         hbm = float(peaks["hbm_gbs"])

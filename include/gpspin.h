@@ -233,8 +233,9 @@ int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_ct
 /* The tiling the handle uses for a pass (dir 0: x-pass, 1: y-pass) in the given
  * mode and its current precision: out[0] CTAs per line group (cluster size),
  * out[1] lines per CTA, out[2] chunk length, out[3] chunks per line, out[4]
- * threads per CTA, out[5] dynamic shared memory bytes, out[6] CTAs per launch.
- * out must hold 7 ints. */
+ * threads per CTA, out[5] dynamic shared memory bytes, out[6] CTAs per launch,
+ * out[7] solve kind: 0 shared-memory line arrays, 1 register-resident chunks
+ * (complex64, chunk length 16, 24 or 32).  out must hold 8 ints. */
 int gp_tiling_info(gp_handle* h, int mode, int dir, int* out);
 
 /* Human-readable text for a gp_status. */

@@ -305,6 +305,9 @@ void fill_common(gp_handle* h, PassArgsT<C>& a)
     a.y0 = -0.5 * h->p.ylen + 0.5 * a.dy;
     a.wx = h->p.wx;
     a.wy = h->p.wy;
+    const double kf[10] = {a.dt * a.c0, a.dt * a.c2, a.dt * a.rabi * 0.70710678118654752440, a.dt, a.x0, a.dx, a.y0,
+                           a.dy, 0.5 * a.dt * a.wx * a.wx, 0.5 * a.dt * a.wy * a.wy};
+    for (int i = 0; i < 10; ++i) a.kf[i] = (float)kf[i];
 }
 
 // Rows can be staged with cp.async.bulk when every row starts on a 16-byte
@@ -873,6 +876,7 @@ int gp_tiling_info(gp_handle* h, int mode, int dir, int* out)
     out[4] = t.threads;
     out[5] = (int)t.smem;
     out[6] = y_blocks(t);
+    out[7] = t.single;
     return GP_OK;
 }
 

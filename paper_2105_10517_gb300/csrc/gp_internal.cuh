@@ -98,6 +98,9 @@ struct PassArgsT {
     double dt, c0, c2, rabi;
     // grid and trap (the complex64 pass evaluates the trap factor inline)
     double x0, dx, y0, dy, wx, wy;
+    // the same constants rounded once to FP32 on the host (complex64 x-pass):
+    // dt c0, dt c2, dt R / sqrt2, dt, x0, dx, y0, dy, dt wx^2 / 2, dt wy^2 / 2
+    float kf[10];
 };
 using PassArgs = PassArgsT<double2>;
 using PassArgsF = PassArgsT<float2>;

@@ -109,6 +109,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err)
     return true;
 }
 
+// Cluster barrier in two halves: an arrive that does not wait and a later wait
+// for every thread of the cluster to have arrived.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
+
 // Stages row segments base + c * plane + (line0 + r) * L + k0 .. + len for
 // r < nl, c < 3 into dst[(r * 3 + c) * stride].  Segments and destination rows
 // must be 16-byte aligned and a multiple of 16 bytes long.
@@ -717,8 +722,11 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
             }
         }
     }
-    // no CTA of the cluster may leave while its carries can still be read
-    group_sync(T);
+    // No CTA of the cluster may leave while its carries can still be read: the
+    // arrive (no more remote reads here) is matched by cluster_wait() at the
+    // end of the pass, so the CTA's store phase overlaps the barrier.
+    if (T.S > 1) cluster_arrive();
+    __syncthreads();  // psi' visible to the whole CTA
 }
 
 // Solve of the CTA's lines: the register-resident form when the kernel is
@@ -774,6 +782,9 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     // barrier -- the other CTA of its cluster waits on them -- but writes nothing.
     ConvCoef<C> cc{};
     if (M > 0 && A.do_solve) cc = load_conv(A.coef + (size_t)line0 * 3, P);
+    // pending normalisation, loaded before the staging wait (complex64 pass)
+    double sd = 0.0;
+    if constexpr (sizeof(R) == 4) sd = *A.scale;
     // with one line array (M > 0) the chunks are staged in place
     bool ok = true;
     if (T.bulk && Ll > 0) {
@@ -783,30 +794,43 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
             ok = stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, Ll, &mbar, A.err);
     }
 
-    // Per-CTA constants, computed once by thread 0 (FP64 work is costly on this
-    // part even inside the complex64 pass) and broadcast through shared memory.
+    // Pointwise constants.  The complex64 pass takes them rounded to FP32 on the
+    // host and converts only the pending normalisation in each thread (FP64
+    // instructions are costly on this part even inside the complex64 pass); the
+    // complex128 pass computes them once in thread 0 and broadcasts them.
     struct KC {
         PConstT<R> k;
         R fx0, fdx, fy0, fdy, hx, hy;  // grid and trap constants (complex64 pass)
     };
-    __shared__ KC kc;
-    if (threadIdx.x == 0) {
-        const double s = *A.scale;
-        kc.k.dtc0 = R(A.dt * A.c0 * s * s);
-        kc.k.dtc2 = R(A.dt * A.c2 * s * s);
-        kc.k.dtr = R(A.dt * A.rabi * 0.70710678118654752440);
-        kc.k.s = R(s);
-        kc.k.dt = R(A.dt);
-        kc.fx0 = R(A.x0);
-        kc.fdx = R(A.dx);
-        kc.fy0 = R(A.y0);
-        kc.fdy = R(A.dy);
-        kc.hx = R(0.5 * A.dt * A.wx * A.wx);
-        kc.hy = R(0.5 * A.dt * A.wy * A.wy);
+    KC kk;
+    if constexpr (sizeof(R) == 4) {
+        const float s = (float)sd;
+        kk.k.dtc0 = A.kf[0] * s * s;
+        kk.k.dtc2 = A.kf[1] * s * s;
+        kk.k.dtr = A.kf[2];
+        kk.k.s = s;
+        kk.k.dt = A.kf[3];
+        kk.fx0 = A.kf[4];
+        kk.fdx = A.kf[5];
+        kk.fy0 = A.kf[6];
+        kk.fdy = A.kf[7];
+        kk.hx = A.kf[8];
+        kk.hy = A.kf[9];
+    } else {
+        __shared__ KC kc;
+        if (threadIdx.x == 0) {
+            sd = *A.scale;
+            kc.k.dtc0 = A.dt * A.c0 * sd * sd;
+            kc.k.dtc2 = A.dt * A.c2 * sd * sd;
+            kc.k.dtr = A.dt * A.rabi * 0.70710678118654752440;
+            kc.k.s = sd;
+            kc.k.dt = A.dt;
+        }
+        __syncthreads();
+        kk = kc;
     }
-    __syncthreads();
-    const PConstT<R> k = kc.k;
-    const struct { R fx0, fdx, fy0, fdy, hx, hy; } tk = {kc.fx0, kc.fdx, kc.fy0, kc.fdy, kc.hx, kc.hy};
+    const PConstT<R> k = kk.k;
+    const KC& tk = kk;
     const FastDiv div_len(Ll), div_nl(nl);
     const SPos spos(T);
     const int Lp = T.Lp;
@@ -861,6 +885,9 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         A.out[o] = xp;
         A.out[plane + o] = x0;
         A.out[2 * plane + o] = xm;
+    }
+    if constexpr (M > 0) {
+        if (T.S > 1) cluster_wait();  // the cluster's CTAs have read this CTA's carries
     }
 }
 
@@ -1012,6 +1039,9 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
             for (int w = 0; w < nw; ++w) t += wsum[w];
             A.partials[cta] = t;
         }
+    }
+    if constexpr (M > 0) {
+        if (T.S > 1) cluster_wait();  // the cluster's CTAs have read this CTA's carries
     }
 }
 

@@ -324,10 +324,10 @@ class Solver:
         """Tiling of the x- and y-pass: dicts of cluster size, lines per CTA, chunk length..."""
         out = {}
         for d, name in ((0, "xpass"), (1, "ypass")):
-            v = (ctypes.c_int * 7)()
+            v = (ctypes.c_int * 8)()
             _check(load().gp_tiling_info(self._h, int(mode), d, v), "gp_tiling_info")
             out[name] = dict(cluster=v[0], lines_per_cta=v[1], chunk=v[2], chunks=v[3], threads=v[4], smem=v[5],
-                             ctas=v[6])
+                             ctas=v[6], register_solve=bool(v[7]))
         return out
 
     def observables(self):
