@@ -48,7 +48,13 @@ INST_PER_SITE = {"xpass": 165, "ypass": 63}
 BYTES_PER_SITE_PASS = 96
 # DRAM traffic of one launch from an ncu capture (profiles/), keyed by kernel
 # and valid only while the kernel source is unchanged (sha256 prefix).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/*.md)
+    "xpass_kernel<0, double2> vortex512": (16204032, "126d0108d0b4da13"),
+    "ypass_kernel<0, double2> vortex512": (16175872, "126d0108d0b4da13"),
+    "xpass_kernel_reg<0, float2, 32> precision2048": (105447168 + 55776256, "126d0108d0b4da13"),
+    "ypass_kernel_reg<0, float2, 32> precision2048": (105490176 + 56463360, "126d0108d0b4da13"),
+}
 
 L2_FLUSH_BYTES = 256 << 20
 
