@@ -640,6 +640,15 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
                 v = cfnma(Co->g[k1], v, cmul(Co->inv[k1], mkc<C>(d.z, d.w)));
                 y[t + 1] = t + 1 < len ? v : zero;
             }
+        } else if (len == M) {  // every chunk but a line's last
+#pragma unroll
+            for (int t = 0; t < M; t += 2) {
+                const float4 d = p4[t / 2];
+                v = cfnma(g_c, v, cmul(inv_c, mkc<C>(d.x, d.y)));
+                y[t] = v;
+                v = cfnma(g_c, v, cmul(inv_c, mkc<C>(d.z, d.w)));
+                y[t + 1] = v;
+            }
         } else {
 #pragma unroll
             for (int t = 0; t < M; t += 2) {
@@ -662,10 +671,9 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
                 C pw = mg;
 #pragma unroll
                 for (int t = 0; t < M; ++t) {
-                    if (t < nf) {
-                        y[t] = cfma(pw, yc, y[t]);
-                        pw = cmul(pw, mg);
-                    }
+                    if (t >= nf) break;  // one exit branch instead of a predicate per row
+                    y[t] = cfma(pw, yc, y[t]);
+                    pw = cmul(pw, mg);
                 }
             } else {
 #pragma unroll
@@ -700,10 +708,9 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
                 C pw = mc;
 #pragma unroll
                 for (int t = M - 1; t >= 0; --t) {
-                    if (t >= M - F) {
-                        y[t] = cfma(pw, wc, y[t]);
-                        pw = cmul(pw, mc);
-                    }
+                    if (t < M - F) break;
+                    y[t] = cfma(pw, wc, y[t]);
+                    pw = cmul(pw, mc);
                 }
             } else {
 #pragma unroll
@@ -714,12 +721,11 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
         // psi' = 2 w - phi, two points per 16-byte access (len is even)
 #pragma unroll
         for (int t = 0; t < M; t += 2) {
-            if (t < len) {
-                float4* p4 = reinterpret_cast<float4*>(pa) + t / 2;
-                const float4 d = *p4;
-                *p4 = make_float4(fma(R(2), y[t].x, -d.x), fma(R(2), y[t].y, -d.y), fma(R(2), y[t + 1].x, -d.z),
-                                  fma(R(2), y[t + 1].y, -d.w));
-            }
+            if (t >= len) break;
+            float4* p4 = reinterpret_cast<float4*>(pa) + t / 2;
+            const float4 d = *p4;
+            *p4 = make_float4(fma(R(2), y[t].x, -d.x), fma(R(2), y[t].y, -d.y), fma(R(2), y[t + 1].x, -d.z),
+                              fma(R(2), y[t + 1].y, -d.w));
         }
     }
     // No CTA of the cluster may leave while its carries can still be read: the

@@ -6,6 +6,9 @@
                                                             # 10000 real-time steps: norm and magnetisation drift
   python -m paper_2105_10517_gb300.workloads precision2048  # 2048^2: FP32 storage then an FP64 refinement block
                                                             # against an all-FP64 run from the same seed
+  python -m paper_2105_10517_gb300.workloads figs1_ferro    # the Fig. S1 procedure: Omega = 0 ground state from the
+  python -m paper_2105_10517_gb300.workloads figs1_antiferro  # centre-vortex guess, continued to Omega = 0.3, then
+                                                            # 50 time units of real time from that ground state
 
 Every step runs in the CUDA library; this module only sequences the calls and
 computes summary numbers of the fetched states (vortex counts, errors).
@@ -49,6 +52,82 @@ def vortex512(steps=None):
     return out
 
 
+def imag_to_convergence(s, cap, tol=1e-9, block=100):
+    """Imaginary time in blocks until |E_k - E_{k-1}| < tol between blocks or
+    `cap` steps; returns (steps, converged)."""
+    e_last, k = None, 0
+    while k < cap:
+        s.propagate(block, gpspin.IMAG)
+        k += block
+        e = s.observables()["energy"]
+        if e_last is not None and abs(e - e_last) < tol:
+            return k, True
+        e_last = e
+    return k, False
+
+
+# Fig. S1 (Supplementary Material) and the text after it: gamma = 0.5, Omega = 0.3,
+# the two condensates of the interaction-constant paragraph (labels as in that
+# paragraph: 87Rb c2 < 0 ferromagnetic, 23Na c2 > 0 antiferromagnetic), DX = 0.1,
+# DT = 0.1 DX^2 in imaginary and 0.025 DX^2 in real time, 50 time units of real
+# time.  Centre charges of the non-rotating SO-coupled ground states, upper sign
+# Rashba: (-+1, 0, +-1) antiferromagnetic, (0, +-1, +-2) ferromagnetic.
+FIGS1 = {
+    "ferro": dict(c0=669.0, c2=-3.1, winding={1: (0, 1, 2), 2: (0, -1, -2)}),
+    "antiferro": dict(c0=482.0, c2=15.0, winding={1: (-1, 0, 1), 2: (1, 0, -1)}),
+}
+
+
+def figs1(kind="ferro", so_type=1, n=256, dx=0.1, omega=0.3, gamma=0.5, imag_cap=100000, tol=1e-9,
+          real_time=50.0, report_every=10.0):
+    """The Fig. S1 procedure, Omega-continuation included.
+
+    1. Imaginary time at Omega = 0 from the centre-vortex initial guess, to
+       convergence.
+    2. Imaginary time at Omega = 0.3 (-0.3 for Dresselhaus, the mirror
+       statement), continued from stage 1's state.
+    3. Real time for `real_time` units from stage 2's ground state.
+
+    Reports E, mu, the centre charges and the vortex counts of every stage, and
+    the norm and magnetisation drift of stage 3.  Qualitative: the figure's
+    densities are not in the paper text."""
+    cfg = FIGS1[kind]
+    length = n * dx
+    dt_imag, dt_real = 0.1 * dx * dx, 0.025 * dx * dx
+    om = omega if so_type == 1 else -omega
+    p = dict(nx=n, ny=n, xlen=length, ylen=length, dt=dt_imag, c0=cfg["c0"], c2=cfg["c2"], omeg=0.0,
+             so_type=so_type, gamma=gamma, rabi=0.0)
+    x, y = inputs.grid(n, n, length, length)
+    out = {"workload": "figs1_" + kind, "so_type": so_type, "n": n, "dx": dx, "gamma": gamma, "omega": om}
+
+    def stage(s):
+        psi = s.get_state()
+        return dict(_obs(s), centre_charges=[diagnostics.central_winding(psi[c], x, y, 1.5) for c in range(3)],
+                    vortices=diagnostics.vortex_counts(psi))
+
+    t = time.perf_counter()
+    with gpspin.Solver(p) as s:
+        s.init_winding((1 / 3, 1 / 3, 1 / 3), winding=cfg["winding"][so_type], seed=3, phase_noise=1e-3)
+        k, conv = imag_to_convergence(s, imag_cap, tol)
+        out["omega0"] = dict(stage(s), imag_steps=k, converged=conv)
+        s.set_params(dict(p, omeg=om))
+        k, conv = imag_to_convergence(s, imag_cap, tol)
+        out["omega_rot"] = dict(stage(s), imag_steps=k, converged=conv)
+        s.set_params(dict(p, omeg=om, dt=dt_real))
+        o0 = s.observables()
+        blk = int(round(report_every / dt_real))
+        drift = []
+        for b in range(int(round(real_time / report_every))):
+            s.propagate(blk, gpspin.REAL)
+            o = s.observables()
+            drift.append(dict(time=(b + 1) * report_every, norm_drift=o["norm_total"] - o0["norm_total"],
+                              magnetization=o["magnetization"], energy=o["energy"]))
+        out["real_time"] = drift
+        out["real_final"] = stage(s)
+    out["wall_s"] = time.perf_counter() - t
+    return out
+
+
 def quench1024(imag_cap=20000, tol=1e-9, real_steps=None):
     c = inputs.CONFIGS["quench1024"]
     p = inputs.physics(c)
@@ -57,15 +136,8 @@ def quench1024(imag_cap=20000, tol=1e-9, real_steps=None):
     t = time.perf_counter()
     with gpspin.Solver(p) as s:
         s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
-        e_last, k = None, 0
-        while k < imag_cap:
-            s.propagate(100, gpspin.IMAG)
-            k += 100
-            e = s.observables()["energy"]
-            if e_last is not None and abs(e - e_last) < tol:
-                break
-            e_last = e
-        out["ground_state"] = dict(_obs(s), imag_steps=k, converged=k < imag_cap)
+        k, conv = imag_to_convergence(s, imag_cap, tol)
+        out["ground_state"] = dict(_obs(s), imag_steps=k, converged=conv)
         s.set_params(dict(p, omeg=0.9))  # the quench: tables are rebuilt
         o0 = s.observables()
         drift = []
@@ -81,25 +153,55 @@ def quench1024(imag_cap=20000, tol=1e-9, real_steps=None):
     return out
 
 
-def precision2048(fp32_steps=38000, fp64_steps=2000):
+def precision2048(fp32_steps=38000, fp64_steps=2000, checkpoint=4000):
     c = inputs.CONFIGS["precision2048"]
     p = inputs.physics(c)
     out = {"workload": "precision2048", "fp32_steps": fp32_steps, "fp64_refine_steps": fp64_steps}
+
+    def run(solver, steps, energies, refine=0):
+        # checkpoints every `checkpoint` steps: where the two trajectories part
+        done = 0
+        while done < steps:
+            k = min(checkpoint, steps - done)
+            solver.propagate(k, gpspin.IMAG)
+            done += k
+            energies.append(solver.observables()["energy"])
+        if refine:
+            solver.refine_fp64(refine, gpspin.IMAG)
+            energies.append(solver.observables()["energy"])
+
+    em, ef = [], []
     t = time.perf_counter()
     with gpspin.Solver(dict(p, precision=gpspin.FP32_MIXED)) as m:
         m.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
-        m.propagate(fp32_steps, gpspin.IMAG)
-        m.refine_fp64(fp64_steps, gpspin.IMAG)
+        run(m, fp32_steps, em, refine=fp64_steps)
         pm = m.get_state()
         out["mixed"] = _obs(m)
     out["mixed_wall_s"] = time.perf_counter() - t
     t = time.perf_counter()
     with gpspin.Solver(dict(p, precision=gpspin.FP64)) as f:
         f.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
-        f.propagate(fp32_steps + fp64_steps, gpspin.IMAG)
+        run(f, fp32_steps, ef)
+        f.propagate(fp64_steps, gpspin.IMAG)
+        ef.append(f.observables()["energy"])
         pf = f.get_state()
         out["fp64"] = _obs(f)
     out["fp64_wall_s"] = time.perf_counter() - t
+    steps = [min((i + 1) * checkpoint, fp32_steps) for i in range(len(em) - 1)] + [fp32_steps + fp64_steps]
+    out["rel_dE_by_step"] = [dict(step=k, rel_dE=abs(a - b) / abs(b)) for k, a, b in zip(steps, em, ef)]
+    # Control: FP64 again from the same state perturbed at the level of FP32
+    # rounding (1e-7 max|psi|, seeded).  If its energy parts from the FP64 run as
+    # fast as the mixed run's does, the gap is the sensitivity of the vortex
+    # nucleation, not an error of the FP32 path.
+    ep = []
+    with gpspin.Solver(dict(p, precision=gpspin.FP64)) as g:
+        g.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+        psi0 = g.get_state()
+        noise = inputs.random_state(p["nx"], p["ny"], seed=c["seed"] + 1000, scale=1e-7 * np.max(np.abs(psi0)))
+        g.set_state(psi0 + noise, normalize=True)
+        run(g, 2 * checkpoint, ep)
+    out["fp64_perturbed_1e-7_rel_dE_by_step"] = [dict(step=(i + 1) * checkpoint, rel_dE=abs(a - b) / abs(b))
+                                                 for i, (a, b) in enumerate(zip(ep, ef))]
     out["rel_dE"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"]) / abs(out["fp64"]["energy"])
     out["rel_dmu"] = abs(out["mixed"]["mu"] - out["fp64"]["mu"]) / abs(out["fp64"]["mu"])
     rm, rf = np.abs(pm) ** 2, np.abs(pf) ** 2
@@ -109,7 +211,8 @@ def precision2048(fp32_steps=38000, fp64_steps=2000):
     return out
 
 
-RUNS = {"vortex512": vortex512, "quench1024": quench1024, "precision2048": precision2048}
+RUNS = {"vortex512": vortex512, "quench1024": quench1024, "precision2048": precision2048,
+        "figs1_ferro": lambda: figs1("ferro"), "figs1_antiferro": lambda: figs1("antiferro")}
 
 
 def main(argv=None):

@@ -119,3 +119,20 @@ def test_fp32_full_size_vortex512_step_parity():
         s.propagate(2, IMAG)
         got = s.get_state()
     assert np.max(np.abs(got - want)) <= 2e-6 * np.max(np.abs(want))
+
+
+def test_fp32_full_size_precision2048_autotuned_step_parity():
+    """The 2048^2 complex64 step in the launch configuration bench.py times
+    (autotuned: register-resident solves, clusters of CTAs) against the oracle."""
+    c = inputs.CONFIGS["precision2048"]
+    p = dict(inputs.physics(c), precision=F32)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=c["seed"])
+    want = oracle.propagate(p, psi, 2, IMAG)
+    with gpspin.Solver(p) as s:
+        s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+        s.autotune(IMAG)
+        t = s.tiling(IMAG)
+        assert t["xpass"]["register_solve"] and t["ypass"]["register_solve"]
+        s.propagate(2, IMAG)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 2e-6 * np.max(np.abs(want))
