@@ -50,10 +50,10 @@ BYTES_PER_SITE_PASS = 96
 # and valid only while the kernel source is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/*.md)
-    "xpass_kernel<0, double2> vortex512": (16204032, "126d0108d0b4da13"),
-    "ypass_kernel<0, double2> vortex512": (16175872, "126d0108d0b4da13"),
-    "xpass_kernel_reg<0, float2, 32> precision2048": (105447168 + 55776256, "126d0108d0b4da13"),
-    "ypass_kernel_reg<0, float2, 32> precision2048": (105490176 + 56463360, "126d0108d0b4da13"),
+    "xpass_kernel<0, double2> vortex512": (16204544, "bd10989174646143"),
+    "ypass_kernel<0, double2> vortex512": (16177152, "bd10989174646143"),
+    "xpass_kernel_reg<0, float2, 32> precision2048": (105450752 + 56456704, "bd10989174646143"),
+    "ypass_kernel_reg<0, float2, 32> precision2048": (105460736 + 56197632, "bd10989174646143"),
 }
 
 L2_FLUSH_BYTES = 256 << 20

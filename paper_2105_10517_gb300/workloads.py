@@ -189,19 +189,27 @@ def precision2048(fp32_steps=38000, fp64_steps=2000, checkpoint=4000):
     out["fp64_wall_s"] = time.perf_counter() - t
     steps = [min((i + 1) * checkpoint, fp32_steps) for i in range(len(em) - 1)] + [fp32_steps + fp64_steps]
     out["rel_dE_by_step"] = [dict(step=k, rel_dE=abs(a - b) / abs(b)) for k, a, b in zip(steps, em, ef)]
-    # Control: FP64 again from the same state perturbed at the level of FP32
-    # rounding (1e-7 max|psi|, seeded).  If its energy parts from the FP64 run as
-    # fast as the mixed run's does, the gap is the sensitivity of the vortex
-    # nucleation, not an error of the FP32 path.
+    # Control: FP64 again, from the initial state rounded to complex64 (the
+    # only difference the FP32 run starts with).  If its energy parts from the
+    # FP64 run as the mixed run's does, the gap comes from the sensitivity of the
+    # vortex nucleation to the initial state, not from error in the FP32 steps.
     ep = []
     with gpspin.Solver(dict(p, precision=gpspin.FP64)) as g:
         g.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
         psi0 = g.get_state()
-        noise = inputs.random_state(p["nx"], p["ny"], seed=c["seed"] + 1000, scale=1e-7 * np.max(np.abs(psi0)))
-        g.set_state(psi0 + noise, normalize=True)
+        g.set_state(psi0.astype(np.complex64).astype(np.complex128), normalize=True)
         run(g, 2 * checkpoint, ep)
-    out["fp64_perturbed_1e-7_rel_dE_by_step"] = [dict(step=(i + 1) * checkpoint, rel_dE=abs(a - b) / abs(b))
-                                                 for i, (a, b) in enumerate(zip(ep, ef))]
+    out["fp64_from_fp32_rounded_state_rel_dE_by_step"] = [
+        dict(step=(i + 1) * checkpoint, rel_dE=abs(a - b) / abs(b)) for i, (a, b) in enumerate(zip(ep, ef))]
+    # Control without rotation (Omega = 0: no vortex nucleation to amplify the
+    # rounding of every step): the FP32 steps against FP64 on the same grid.
+    e32, e64 = [], []
+    for prec, acc in ((gpspin.FP32_MIXED, e32), (gpspin.FP64, e64)):
+        with gpspin.Solver(dict(p, omeg=0.0, precision=prec)) as g:
+            g.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+            run(g, 2 * checkpoint, acc)
+    out["no_rotation_fp32_vs_fp64_rel_dE_by_step"] = [
+        dict(step=(i + 1) * checkpoint, rel_dE=abs(a - b) / abs(b)) for i, (a, b) in enumerate(zip(e32, e64))]
     out["rel_dE"] = abs(out["mixed"]["energy"] - out["fp64"]["energy"]) / abs(out["fp64"]["energy"])
     out["rel_dmu"] = abs(out["mixed"]["mu"] - out["fp64"]["mu"]) / abs(out["fp64"]["mu"])
     rm, rf = np.abs(pm) ** 2, np.abs(pf) ** 2
