@@ -191,6 +191,9 @@ __device__ __forceinline__ void group_sync(const LineTiling& T)
 // precision).  The line operator is A = -1/2 D2 + kappa D1 with kappa = i kb;
 // the CN system matrix is I + tau A with tau = dt/2 (imaginary time) or i dt/2
 // (real time): constant sub-diagonal alpha, diagonal beta, super-diagonal gamma'.
+// In imaginary time beta and alpha gamma' = tau^2 (1/(4h^4) + kb^2/(4h^2)) are
+// real, so every pivot is real: the recurrence is run in real arithmetic and the
+// stored inv has a zero imaginary part, which the sweeps use (a real scaling).
 template <typename C>
 __global__ void coef_kernel(LineCoefT<C>* coef, int nlines, int dir, int mode, double h, double line_len,
                             double line_h, double dt, double omeg, double gamma, int eta, int* status)
@@ -209,8 +212,16 @@ __global__ void coef_kernel(LineCoefT<C>* coef, int nlines, int dir, int mode, d
     double2 beta = make_double2(1.0 + tau.x * b, tau.y * b);
     LineCoefT<C>& Co = coef[id];
     double2 cprev = make_double2(0.0, 0.0), glast = cprev;
+    const double ag = alpha.x * gam.x - alpha.y * gam.y;  // real alpha gamma' (imaginary time)
+    double rinv = 0.0;
     for (int k = 0; k < kHead; ++k) {
-        double2 inv = drecip(dsub(beta, cmul(alpha, cprev)));
+        double2 inv;
+        if (mode == 1) {
+            inv = drecip(dsub(beta, cmul(alpha, cprev)));
+        } else {
+            rinv = 1.0 / (beta.x - ag * rinv);
+            inv = make_double2(rinv, 0.0);
+        }
         double2 cp = cmul(gam, inv);
         double2 g = cmul(alpha, inv);
         Co.inv[k] = store_as<C>(inv);
@@ -472,7 +483,17 @@ __device__ __forceinline__ void from_sigma_x(C xp, C x0, C xm, C& a, C& b, C& c)
 // rounding, so no carry has to be propagated sequentially across chunks.
 // Smem: line-channel arrays of stride Lp, chunk q at offset q cs (the strides
 // keep chunk-parallel accesses on distinct banks).
-template <typename C>
+// In imaginary time (MODE 0) the pivots are real and inv scales phi as a real.
+template <int MODE, typename C>
+__device__ __forceinline__ C scale_inv(const C& inv, const C& v)
+{
+    if constexpr (MODE == 0)
+        return mkc<C>(inv.x * v.x, inv.x * v.y);
+    else
+        return cmul(inv, v);
+}
+
+template <int MODE, typename C>
 __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const LineCoefT<C>* coef,
                                                const LineTiling& T, const Part& P)
 {
@@ -512,7 +533,7 @@ __device__ __forceinline__ void chunked_thomas(C* sa, C* sb, C* cf, C* cb, const
                 inv = Co->inv[k];
                 g = Co->g[k];
             }
-            y = cfnma(g, y, cmul(inv, pa[t]));
+            y = cfnma(g, y, scale_inv<MODE>(inv, pa[t]));
             pbf[t] = y;
         }
         cf[lc * Qc + ql] = y;
@@ -599,7 +620,7 @@ __device__ __forceinline__ ConvCoef<C> load_conv(const LineCoefT<C>* coef, const
 // Chunks q >= 1 start at row m >= H + F, past the rows where the factorisation
 // still differs from its limit (H rows) and where the fixup powers matter, so
 // they use the converged coefficients throughout; chunk 0 takes the table rows.
-template <typename C, int M>
+template <int MODE, typename C, int M>
 __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const LineCoefT<C>* coef,
                                                    const ConvCoef<C>& cc, const LineTiling& T, const Part& P)
 {
@@ -635,27 +656,27 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
             for (int t = 0; t < M; t += 2) {
                 const float4 d = p4[t / 2];
                 const int k0 = t < kHead - 1 ? t : kHead - 1, k1 = t + 1 < kHead - 1 ? t + 1 : kHead - 1;
-                v = cfnma(Co->g[k0], v, cmul(Co->inv[k0], mkc<C>(d.x, d.y)));
+                v = cfnma(Co->g[k0], v, scale_inv<MODE>(Co->inv[k0], mkc<C>(d.x, d.y)));
                 y[t] = t < len ? v : zero;
-                v = cfnma(Co->g[k1], v, cmul(Co->inv[k1], mkc<C>(d.z, d.w)));
+                v = cfnma(Co->g[k1], v, scale_inv<MODE>(Co->inv[k1], mkc<C>(d.z, d.w)));
                 y[t + 1] = t + 1 < len ? v : zero;
             }
         } else if (len == M) {  // every chunk but a line's last
 #pragma unroll
             for (int t = 0; t < M; t += 2) {
                 const float4 d = p4[t / 2];
-                v = cfnma(g_c, v, cmul(inv_c, mkc<C>(d.x, d.y)));
+                v = cfnma(g_c, v, scale_inv<MODE>(inv_c, mkc<C>(d.x, d.y)));
                 y[t] = v;
-                v = cfnma(g_c, v, cmul(inv_c, mkc<C>(d.z, d.w)));
+                v = cfnma(g_c, v, scale_inv<MODE>(inv_c, mkc<C>(d.z, d.w)));
                 y[t + 1] = v;
             }
         } else {
 #pragma unroll
             for (int t = 0; t < M; t += 2) {
                 const float4 d = p4[t / 2];
-                v = cfnma(g_c, v, cmul(inv_c, mkc<C>(d.x, d.y)));
+                v = cfnma(g_c, v, scale_inv<MODE>(inv_c, mkc<C>(d.x, d.y)));
                 y[t] = t < len ? v : zero;
-                v = cfnma(g_c, v, cmul(inv_c, mkc<C>(d.z, d.w)));
+                v = cfnma(g_c, v, scale_inv<MODE>(inv_c, mkc<C>(d.z, d.w)));
                 y[t + 1] = t + 1 < len ? v : zero;
             }
         }
@@ -737,14 +758,14 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
 
 // Solve of the CTA's lines: the register-resident form when the kernel is
 // compiled for the tiling's chunk length M, the shared-memory form for M = 0.
-template <typename C, int M>
+template <int MODE, typename C, int M>
 __device__ __forceinline__ void solve_lines(C* sa, C* sb, C* cf, C* cb, const LineCoefT<C>* coef,
                                             const ConvCoef<C>& cc, const LineTiling& T, const Part& P)
 {
     if constexpr (M > 0)
-        chunked_thomas_reg<C, M>(sa, cf, cb, coef, cc, T, P);
+        chunked_thomas_reg<MODE, C, M>(sa, cf, cb, coef, cc, T, P);
     else
-        chunked_thomas(sa, sb, cf, cb, coef, T, P);
+        chunked_thomas<MODE>(sa, sb, cf, cb, coef, T, P);
 }
 
 // Division by a per-CTA constant d as a multiply-high: q = floor(k * ceil(2^32 / d) / 2^32)
@@ -879,7 +900,7 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         dst[2 * Lp] = m;
     }
     __syncthreads();
-    if (A.do_solve) solve_lines<C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P);
+    if (A.do_solve) solve_lines<MODE, C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P);
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, i = k0 + kl, j = line0 + r;
@@ -995,7 +1016,7 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
         }
     }
     __syncthreads();
-    if (A.do_solve) solve_lines<C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P);
+    if (A.do_solve) solve_lines<MODE, C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P);
     R acc = R(0), acc3[3] = {R(0), R(0), R(0)};
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, j = k0 + kl, i = line0 + r;
