@@ -106,6 +106,19 @@ int gp_set_state(gp_handle* h, const double* psi_host, int normalize);
  * applied to the copy. */
 int gp_get_state(gp_handle* h, double* psi_out);
 
+/* From host state to host state in one call: the same result as
+ * gp_set_state(h, psi_in, 0), gp_propagate(h, nsteps, mode) and
+ * gp_get_state(h, psi_out), and the handle holds the new state afterwards.
+ * psi_in and psi_out are complex128 psi[3][ny][nx] host buffers owned by the
+ * caller (they may be the same buffer); the call returns once psi_out is
+ * written.  On a GP_FP64 handle, when the device can address the buffers
+ * (pinned memory, or pageable memory on systems where the GPU reads host page
+ * tables, such as NVLink-C2C hosts) and they are 16-byte aligned, the first
+ * x-pass reads psi_in directly, so the host-to-device transfer overlaps the
+ * pass's work, and the normalised result is written straight into psi_out;
+ * otherwise the three calls above are made.  Errors as for those calls. */
+int gp_propagate_host(gp_handle* h, const double* psi_in, long long nsteps, int mode, double* psi_out);
+
 /* Device initial state: psi_c = sqrt(frac[c]) pi^{-1/2} exp(-(x^2+y^2)/2)
  * exp(i phi_c(x,y)), phi = phase_noise (2u - 1), u = top 53 bits of
  * splitmix64(seed ^ ((c ny + j) nx + i)) times 2^-53; then normalised to 1. */

@@ -715,6 +715,68 @@ int gp_refine_fp64(gp_handle* h, long long nsteps, int mode)
     return check_flags(h);
 }
 
+// Device address through which kernels can read or write the host buffer p
+// (16-byte aligned, complex128): pinned memory through its mapping, pageable
+// memory where the device reaches it through the host page tables.  nullptr if
+// neither holds: the caller then copies with cudaMemcpyAsync.
+static double2* device_view(const double* p)
+{
+    if (reinterpret_cast<uintptr_t>(p) % 16) return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeHost) return static_cast<double2*>(at.devicePointer);
+    if (at.type != cudaMemoryTypeUnregistered) return nullptr;
+    int dev = 0, pageable = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return pageable ? reinterpret_cast<double2*>(const_cast<double*>(p)) : nullptr;
+}
+
+int gp_propagate_host(gp_handle* h, const double* psi_in, long long nsteps, int mode, double* psi_out)
+{
+    if (!h || !psi_in || !psi_out || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
+    const double2* din = device_view(psi_in);
+    double2* dout = device_view(psi_out);
+    const bool mc = mode == GP_IMAG && h->mcon;
+    if (!din || h->active != GP_FP64 || nsteps == 0) {
+        int st = gp_set_state(h, psi_in, 0);
+        if (st == GP_OK) st = gp_propagate(h, nsteps, mode);
+        return st == GP_OK ? gp_get_state(h, psi_out) : st;
+    }
+    // the state of gp_set_state(h, psi_in, 0): nothing pending
+    LK(launch_set_scalar(h->scal, 1.0, h->stream));
+    h->scale_pending = false;
+    int st = ensure_coef(h, mode);
+    if (st) return st;
+    const CoefSet& cs = h->coef[mode];
+    const int gy = y_blocks(cs.ty);
+    if (gy * (mc ? 3 : 1) > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
+    if (mc && (gamma_of(h->p) != 0.0 || h->p.rabi != 0.0)) return GP_ERR_ARG;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    // first step: the x-pass loads the host state directly (plain loads; bulk
+    // copies are kept for device memory), overlapping the transfer with its work
+    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+    ax.in = din;
+    ax.t.bulk = 0;
+    if (mode == GP_IMAG) ay.partials = h->partials;
+    ay.mcomp = mc;
+    if ((st = enqueue_steps(h, mode, ax, ay, gy, 1))) return st;
+    if (mode == GP_IMAG && !mc) h->scale_pending = true;
+    h->steps += 1;
+    if (nsteps > 1 && (st = propagate_active(h, nsteps - 1, mode))) return st;
+    if ((st = check_flags(h))) return st;
+    if (!dout) return gp_get_state(h, psi_out);
+    // the normalised result is written straight into the caller's buffer
+    LK(launch_scaled_copy(dout, h->psi, n_elems(h), h->scal, h->stream));
+    return sync_status(h);
+}
+
 int gp_profile_step(gp_handle* h, int mode, float* ms_out)
 {
     if (!h || !ms_out || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;

@@ -32,7 +32,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-           "gp_init_winding", "gp_set_magnetization", "gp_propagate", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
+           "gp_init_winding", "gp_set_magnetization", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
            "gp_tiling_info", "gp_set_tiling",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_strerror"]
@@ -146,6 +146,7 @@ def load():
     lib.gp_set_magnetization.argtypes = [vp, ip, ctypes.c_double]
     lib.gp_set_magnetization.restype = ctypes.c_int
     lib.gp_propagate.argtypes = [vp, ctypes.c_longlong, ip]
+    lib.gp_propagate_host.argtypes = [vp, dp, ctypes.c_longlong, ip, dp]
     lib.gp_refine_fp64.argtypes = [vp, ctypes.c_longlong, ip]
     lib.gp_observables.argtypes = [vp, ctypes.POINTER(Obs)]
     lib.gp_apply_substep.argtypes = [vp, ip, ip]
@@ -276,6 +277,19 @@ class Solver:
             raise ValueError("get_state: out must be a C-contiguous complex128 array")
         ptr, keep = self._host_ptr(out, "get_state")
         _check(load().gp_get_state(self._h, ptr), "gp_get_state")
+        return out
+
+    def propagate_host(self, psi_in, nsteps, mode=IMAG, out=None):
+        """set_state(psi_in) + propagate(nsteps, mode) + get_state(out) in one
+        library call (the first pass reads psi_in directly where the device can)."""
+        if out is None:
+            out = np.empty((3, self.ny, self.nx), dtype=np.complex128)
+        elif not hasattr(out, "data_ptr") and (not isinstance(out, np.ndarray) or out.dtype != np.complex128
+                                               or not out.flags.c_contiguous):
+            raise ValueError("propagate_host: out must be a C-contiguous complex128 array")
+        pin, keep_in = self._host_ptr(psi_in, "propagate_host")
+        pout, keep_out = self._host_ptr(out, "propagate_host")
+        _check(load().gp_propagate_host(self._h, pin, int(nsteps), int(mode), pout), "gp_propagate_host")
         return out
 
     def init_gaussian(self, frac=(0.25, 0.5, 0.25), seed=1, phase_noise=1e-3):
