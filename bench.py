@@ -42,10 +42,10 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # from the kernel arithmetic, without the chunk fixups of the parallel solve.
 # In imaginary time the Thomas pivots are real, so a channel point costs 22 flops:
 # forward 2 (real scaling) + 8, back substitution 8, psi' = 2w - phi 4.
-#   x-pass: P 160 (63 FMA, 31 MUL, 3 ADD) + U_y^dag 16 + Thomas 3 x 22 + U_x^dag U_y 14
+#   x-pass: P 156 (63 FMA, 27 MUL, 3 ADD) + U_y^dag 16 + Thomas 3 x 22 + U_x^dag U_y 14
 #   y-pass: Thomas 3 x 22 + U_x 16 + |psi|^2 partial sums 12
-FLOPS_PER_SITE = {"xpass": 256, "ypass": 94}
-INST_PER_SITE = {"xpass": 159, "ypass": 57}
+FLOPS_PER_SITE = {"xpass": 252, "ypass": 94}
+INST_PER_SITE = {"xpass": 155, "ypass": 57}
 # Algorithmic HBM bytes per site and pass: read and write 3 complex128 values.
 BYTES_PER_SITE_PASS = 96
 # DRAM traffic of one launch from an ncu capture (profiles/), keyed by kernel

@@ -386,9 +386,12 @@ __device__ __forceinline__ void scalar_cis(float x, float& cs, float& sn) { sinc
 
 // ev: trap factor from the tables (complex128 pass); tv: dt V added to the
 // scalar exponent instead (complex64 pass, ev = 1, one expf/sincosf per site).
+// In imaginary time the scalar factor s ev exp(-x) is real and is returned in ps,
+// not applied: the basis rotation that follows takes it in its two constants.
+// In real time it is applied here and ps = 1.
 template <int MODE, typename C>
 __device__ __forceinline__ void pointwise(C& a, C& b, C& c, C ev, typename RealOf<C>::type tv,
-                                          const PConstT<typename RealOf<C>::type>& k)
+                                          const PConstT<typename RealOf<C>::type>& k, typename RealOf<C>::type& ps)
 {
     typedef typename RealOf<C>::type R;
     R rp = fma(a.x, a.x, a.y * a.y);
@@ -420,23 +423,25 @@ __device__ __forceinline__ void pointwise(C& a, C& b, C& c, C ev, typename RealO
         a = cmul(ph, ta);
         b = cmul(ph, tb);
         c = cmul(ph, tc);
+        ps = R(1);
     } else {
-        R ph = k.s * ev.x * scalar_exp(x);
-        a = mkc<C>(ph * fma(-s1, va.x, fma(s2, wa.x, a.x)), ph * fma(-s1, va.y, fma(s2, wa.y, a.y)));
-        b = mkc<C>(ph * fma(-s1, vb.x, fma(s2, wb.x, b.x)), ph * fma(-s1, vb.y, fma(s2, wb.y, b.y)));
-        c = mkc<C>(ph * fma(-s1, vc.x, fma(s2, wc.x, c.x)), ph * fma(-s1, vc.y, fma(s2, wc.y, c.y)));
+        ps = k.s * ev.x * scalar_exp(x);
+        a = mkc<C>(fma(-s1, va.x, fma(s2, wa.x, a.x)), fma(-s1, va.y, fma(s2, wa.y, a.y)));
+        b = mkc<C>(fma(-s1, vb.x, fma(s2, wb.x, b.x)), fma(-s1, vb.y, fma(s2, wb.y, b.y)));
+        c = mkc<C>(fma(-s1, vc.x, fma(s2, wc.x, c.x)), fma(-s1, vc.y, fma(s2, wc.y, c.y)));
     }
 }
 
 // --------------------------------------------------------- basis rotations --
-// phi = U_y^dagger psi: Sigma_y eigen-channels lambda = +1, 0, -1 with
-// eigenvectors (1, i sqrt2, -1)/2, (1, 0, 1)/sqrt2, (1, -i sqrt2, -1)/2.
+// phi = U_y^dagger (ps psi): Sigma_y eigen-channels lambda = +1, 0, -1 with
+// eigenvectors (1, i sqrt2, -1)/2, (1, 0, 1)/sqrt2, (1, -i sqrt2, -1)/2, and a
+// real scale ps folded into the constants.
 template <typename C>
-__device__ __forceinline__ void to_sigma_y(C a, C b, C c, C& p, C& z, C& m)
+__device__ __forceinline__ void to_sigma_y(C a, C b, C c, typename RealOf<C>::type ps, C& p, C& z, C& m)
 {
     typedef typename RealOf<C>::type R;
-    const R rs2 = R(0.70710678118654752440);
-    R dx = R(0.5) * (a.x - c.x), dy = R(0.5) * (a.y - c.y);
+    const R rs2 = R(0.70710678118654752440) * ps, half = R(0.5) * ps;
+    R dx = half * (a.x - c.x), dy = half * (a.y - c.y);
     p = mkc<C>(fma(rs2, b.y, dx), fma(-rs2, b.x, dy));
     m = mkc<C>(fma(-rs2, b.y, dx), fma(rs2, b.x, dy));
     z = mkc<C>(rs2 * (a.x + c.x), rs2 * (a.y + c.y));
@@ -876,24 +881,23 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
             b = A.in[plane + o];
             c = A.in[2 * plane + o];
         }
+        R ps;
         if (A.do_p) {
             if constexpr (sizeof(R) == 8) {
                 // trap factor from the per-axis tables (real in imaginary time)
                 C ev = MODE == 1 ? cmul(A.ex[i], A.ey[j]) : mkc<C>(A.ex[i].x * A.ey[j].x, R(0));
-                pointwise<MODE>(a, b, c, ev, R(0), k);
+                pointwise<MODE>(a, b, c, ev, R(0), k, ps);
             } else {
                 // complex64: dt V joins the scalar exponent (no table loads)
                 const R xx = fma(R(i), tk.fdx, tk.fx0), yy = fma(R(j), tk.fdy, tk.fy0);
                 const R tv = fma(tk.hx * xx, xx, tk.hy * yy * yy);
-                pointwise<MODE>(a, b, c, mkc<C>(R(1), R(0)), tv, k);
+                pointwise<MODE>(a, b, c, mkc<C>(R(1), R(0)), tv, k, ps);
             }
         } else {
-            a = mkc<C>(k.s * a.x, k.s * a.y);
-            b = mkc<C>(k.s * b.x, k.s * b.y);
-            c = mkc<C>(k.s * c.x, k.s * c.y);
+            ps = k.s;  // channels pass through, with the pending normalisation
         }
         C p, z, m;
-        to_sigma_y(a, b, c, p, z, m);
+        to_sigma_y(a, b, c, ps, p, z, m);
         C* dst = sa + r * 3 * Lp + spos(kl);
         dst[0] = p;
         dst[Lp] = z;
