@@ -52,10 +52,10 @@ BYTES_PER_SITE_PASS = 96
 # and valid only while the kernel source is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/*.md)
-    "xpass_kernel<0, double2> vortex512": (16204544, "bd10989174646143"),
-    "ypass_kernel<0, double2> vortex512": (16177152, "bd10989174646143"),
-    "xpass_kernel_reg<0, float2, 32> precision2048": (105450752 + 56456704, "bd10989174646143"),
-    "ypass_kernel_reg<0, float2, 32> precision2048": (105460736 + 56197632, "bd10989174646143"),
+    "xpass_kernel<0, double2> vortex512": (16203776, "47696c67ef03b63f"),
+    "ypass_kernel<0, double2> vortex512": (16175616, "47696c67ef03b63f"),
+    "xpass_kernel_reg<0, float2, 32> precision2048": (105475584 + 56702720, "47696c67ef03b63f"),
+    "ypass_kernel_reg<0, float2, 32> precision2048": (105490944 + 56187136, "47696c67ef03b63f"),
 }
 
 L2_FLUSH_BYTES = 256 << 20
