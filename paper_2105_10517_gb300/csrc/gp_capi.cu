@@ -133,7 +133,9 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
         }
     auto up = [](size_t b) { return (b + 127) / 128 * 128; };
     const size_t line_bytes = up(3 * R * Lp * elem);
-    const size_t smem = line_bytes * (single ? 1 : 2) + 2 * up(3 * R * Qc * elem);
+    // carries: cf, cb (3R Qc each) and, after cb, the two 3R-slot halos that
+    // the cluster neighbours push into (register-resident solve)
+    const size_t smem = line_bytes * (single ? 1 : 2) + 2 * up(3 * R * Qc * elem) + up(2 * 3 * R * elem);
     if (smem > 227 * 1024) return GP_ERR_UNSUPPORTED;
     t->L = L;
     t->nlines = nlines;

@@ -114,6 +114,38 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err)
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 
+// Point-to-point carries between neighbouring CTAs of a cluster: the producer
+// stores the value into the neighbour's shared memory and arrives on the
+// neighbour's mbarrier (release, cluster scope); the consumer waits on its own
+// mbarrier (acquire, cluster scope).  The wait is bounded: a time-out sets status
+// bit 8 and goes on.
+__device__ __forceinline__ uint32_t cluster_map(const void* p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void push_carry(float2 v, float2* slot, uint64_t* bar, uint32_t rank)
+{
+    const uint32_t a = cluster_map(slot, rank), b = cluster_map(bar, rank);
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(b) : "memory");
+}
+
+__device__ __forceinline__ void wait_carry(uint64_t* bar, int* err)
+{
+    uint32_t ok = 0;
+    for (int it = 0; it < kWaitTries && !ok; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar))
+            : "memory");
+    if (!ok && err) atomicOr(err, 8);
+}
+
 // Stages row segments base + c * plane + (line0 + r) * L + k0 .. + len for
 // r < nl, c < 3 into dst[(r * 3 + c) * stride].  Segments and destination rows
 // must be 16-byte aligned and a multiple of 16 bytes long.
@@ -627,7 +659,8 @@ __device__ __forceinline__ ConvCoef<C> load_conv(const LineCoefT<C>* coef, const
 // they use the converged coefficients throughout; chunk 0 takes the table rows.
 template <int MODE, typename C, int M>
 __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const LineCoefT<C>* coef,
-                                                   const ConvCoef<C>& cc, const LineTiling& T, const Part& P)
+                                                   const ConvCoef<C>& cc, const LineTiling& T, const Part& P,
+                                                   C* hf, C* hb, uint64_t* cbar, int* err)
 {
     typedef typename RealOf<C>::type R;
     static_assert(sizeof(C) == 8 && M % 2 == 0, "pairs of complex64 per 16-byte shared-memory access");
@@ -641,13 +674,9 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
     const int len = max(0, min(M, L - q * M));
     const LineCoefT<C>* Co = coef + lc;
     C* __restrict__ pa = sa + lc * Lp + ql * T.cs;
-    const C* cf_prev = cf;
-    const C* cb_next = cb;
-    if (T.S > 1) {
-        cg::cluster_group cl = cg::this_cluster();
-        if (P.rank > 0) cf_prev = cl.map_shared_rank(cf, P.rank - 1);
-        if (P.rank < T.S - 1) cb_next = cl.map_shared_rank(cb, P.rank + 1);
-    }
+    // In a cluster the first chunk of a CTA takes its forward carry from the
+    // left neighbour's last chunk (pushed into hf, counted on cbar[0]) and the
+    // last chunk its backward carry from the right neighbour's first (hb, cbar[1]).
     const C zero = mkc<C>(R(0), R(0));
     const C inv_c = cc.inv, g_c = cc.g, cp_c = cc.cp;
     C y[M];
@@ -687,10 +716,20 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
         }
         cf[lc * Qc + ql] = y[M - 1];
     }
-    group_sync(T);
+    if (T.S > 1) {
+        cluster_wait();  // start barrier: the neighbours' mbarriers are initialised
+        if (active && ql == P.nq - 1 && P.rank < T.S - 1) push_carry(y[M - 1], hf + lc, cbar, P.rank + 1);
+    }
+    __syncthreads();
     if (active) {
         if (q > 0) {
-            const C yc = ql > 0 ? cf[lc * Qc + ql - 1] : cf_prev[lc * Qc + Qc - 1];
+            C yc;
+            if (ql > 0) {
+                yc = cf[lc * Qc + ql - 1];
+            } else {  // q > 0 with ql == 0: a cluster rank > 0
+                wait_carry(cbar, err);
+                yc = hf[lc];
+            }
             const int nf = min(F, len);
             if constexpr (sizeof(R) == 4) {
                 const C mg = mkc<C>(-g_c.x, -g_c.y);
@@ -724,11 +763,22 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
             }
         }
         cb[lc * Qc + ql] = y[0];
+        if (T.S > 1 && ql == 0 && P.rank > 0) push_carry(y[0], hb + lc, cbar + 1, P.rank - 1);
     }
-    group_sync(T);
+    // No CTA of the cluster may leave while a neighbour's store into its shared
+    // memory can be in flight: this CTA's stores are done here (arrive), and the
+    // matching cluster_wait() closes the pass, overlapping the store phase.
+    if (T.S > 1) cluster_arrive();
+    __syncthreads();
     if (active) {
         if (q < Q - 1) {  // full chunk (len == M): the last F points take the backward fixup
-            const C wc = ql < P.nq - 1 ? cb[lc * Qc + ql + 1] : cb_next[lc * Qc + 0];
+            C wc;
+            if (ql < P.nq - 1) {
+                wc = cb[lc * Qc + ql + 1];
+            } else {  // the last chunk of a CTA that is not the line's last: rank < S - 1
+                wait_carry(cbar + 1, err);
+                wc = hb[lc];
+            }
             if constexpr (sizeof(R) == 4) {
                 const C mc = mkc<C>(-cp_c.x, -cp_c.y);
                 C pw = mc;
@@ -754,10 +804,6 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
                               fma(R(2), y[t + 1].y, -d.w));
         }
     }
-    // No CTA of the cluster may leave while its carries can still be read: the
-    // arrive (no more remote reads here) is matched by cluster_wait() at the
-    // end of the pass, so the CTA's store phase overlaps the barrier.
-    if (T.S > 1) cluster_arrive();
     __syncthreads();  // psi' visible to the whole CTA
 }
 
@@ -765,10 +811,12 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
 // compiled for the tiling's chunk length M, the shared-memory form for M = 0.
 template <int MODE, typename C, int M>
 __device__ __forceinline__ void solve_lines(C* sa, C* sb, C* cf, C* cb, const LineCoefT<C>* coef,
-                                            const ConvCoef<C>& cc, const LineTiling& T, const Part& P)
+                                            const ConvCoef<C>& cc, const LineTiling& T, const Part& P,
+                                            uint64_t* cbar, int* err)
 {
     if constexpr (M > 0)
-        chunked_thomas_reg<MODE, C, M>(sa, cf, cb, coef, cc, T, P);
+        chunked_thomas_reg<MODE, C, M>(sa, cf, cb, coef, cc, T, P, cb + 3 * T.R * T.Qc, cb + 3 * T.R * (T.Qc + 1),
+                                       cbar, err);
     else
         chunked_thomas<MODE>(sa, sb, cf, cb, coef, T, P);
 }
@@ -797,7 +845,8 @@ struct SPos {
 // --------------------------------------------------------------- x-pass ----
 // One CTA of the x-pass: lines cta*R .. cta*R + R - 1 of instance A.
 template <int MODE, typename C, int M>
-__device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar)
+__device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar,
+                                           uint64_t* cbar)
 {
     typedef typename RealOf<C>::type R;
     const LineTiling& T = A.t;
@@ -814,6 +863,15 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     // barrier -- the other CTA of its cluster waits on them -- but writes nothing.
     ConvCoef<C> cc{};
     if (M > 0 && A.do_solve) cc = load_conv(A.coef + (size_t)line0 * 3, P);
+    if constexpr (M > 0) {
+        if (T.S > 1) {  // carry mbarriers, then the start half of the cluster barrier
+            if (threadIdx.x == 0) {
+                mbar_init(&cbar[0], 3 * nl);
+                mbar_init(&cbar[1], 3 * nl);
+            }
+            cluster_arrive();
+        }
+    }
     // pending normalisation, loaded before the staging wait (complex64 pass)
     double sd = 0.0;
     if constexpr (sizeof(R) == 4) sd = *A.scale;
@@ -904,7 +962,7 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         dst[2 * Lp] = m;
     }
     __syncthreads();
-    if (A.do_solve) solve_lines<MODE, C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P);
+    if (A.do_solve) solve_lines<MODE, C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P, cbar, A.err);
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, i = k0 + kl, j = line0 + r;
@@ -928,7 +986,8 @@ __global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
-    xpass_body<MODE, C, 0>(A, blockIdx.x, smem_raw, mbar);
+    __shared__ uint64_t cbar[2];
+    xpass_body<MODE, C, 0>(A, blockIdx.x, smem_raw, mbar, cbar);
 }
 
 // With the register-resident solve of chunk length M (one-array tilings).  The
@@ -940,7 +999,8 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) xpass_kernel_reg(
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
-    xpass_body<MODE, C, M>(A, blockIdx.x, smem_raw, mbar);
+    __shared__ uint64_t cbar[2];
+    xpass_body<MODE, C, M>(A, blockIdx.x, smem_raw, mbar, cbar);
 }
 
 // Many instances in one launch: CTA b works on item items[b] = (instance, cta)
@@ -950,10 +1010,11 @@ __global__ void __launch_bounds__(512) xpass_batched(const PassArgsT<C>* args, c
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
+    __shared__ uint64_t cbar[2];
     if ((int)blockIdx.x >= *n_items) return;
     const int2 it = items[blockIdx.x];
     const PassArgsT<C> A = args[it.x];
-    xpass_body<MODE, C, 0>(A, it.y, smem_raw, mbar);
+    xpass_body<MODE, C, 0>(A, it.y, smem_raw, mbar, cbar);
 }
 
 // The same with the register-resident solve: every item's tiling is a one-array
@@ -964,10 +1025,11 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
+    __shared__ uint64_t cbar[2];
     if ((int)blockIdx.x >= *n_items) return;
     const int2 it = items[blockIdx.x];
     const PassArgsT<C> A = args[it.x];
-    xpass_body<MODE, C, M>(A, it.y, smem_raw, mbar);
+    xpass_body<MODE, C, M>(A, it.y, smem_raw, mbar, cbar);
 }
 
 // --------------------------------------------------------------- y-pass ----
@@ -975,7 +1037,7 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
 // (a few dozen sites), the CTA then adds the threads' sums in FP64.
 template <int MODE, typename C, int M>
 __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar,
-                                           double* wsum)
+                                           double* wsum, uint64_t* cbar)
 {
     typedef typename RealOf<C>::type R;
     const LineTiling& T = A.t;
@@ -991,6 +1053,15 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     // on a timeout the CTA runs every barrier but writes nothing (see the x-pass)
     ConvCoef<C> cc{};
     if (M > 0 && A.do_solve) cc = load_conv(A.coef + (size_t)line0 * 3, P);
+    if constexpr (M > 0) {
+        if (T.S > 1) {  // carry mbarriers, then the start half of the cluster barrier
+            if (threadIdx.x == 0) {
+                mbar_init(&cbar[0], 3 * nl);
+                mbar_init(&cbar[1], 3 * nl);
+            }
+            cluster_arrive();
+        }
+    }
     // with one line array (M > 0) the chunks are staged in place and need no copy
     bool ok = true;
     if (T.bulk && Ll > 0) {
@@ -1020,7 +1091,7 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
         }
     }
     __syncthreads();
-    if (A.do_solve) solve_lines<MODE, C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P);
+    if (A.do_solve) solve_lines<MODE, C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P, cbar, A.err);
     R acc = R(0), acc3[3] = {R(0), R(0), R(0)};
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, j = k0 + kl, i = line0 + r;
@@ -1081,8 +1152,9 @@ __global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
+    __shared__ uint64_t cbar[2];
     __shared__ double wsum[32];
-    ypass_body<MODE, C, 0>(A, blockIdx.x, smem_raw, mbar, wsum);
+    ypass_body<MODE, C, 0>(A, blockIdx.x, smem_raw, mbar, wsum, cbar);
 }
 
 template <int MODE, typename C, int M>
@@ -1090,8 +1162,9 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) ypass_kernel_reg(
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
+    __shared__ uint64_t cbar[2];
     __shared__ double wsum[32];
-    ypass_body<MODE, C, M>(A, blockIdx.x, smem_raw, mbar, wsum);
+    ypass_body<MODE, C, M>(A, blockIdx.x, smem_raw, mbar, wsum, cbar);
 }
 
 template <int MODE, typename C>
@@ -1099,11 +1172,12 @@ __global__ void __launch_bounds__(512) ypass_batched(const PassArgsT<C>* args, c
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
+    __shared__ uint64_t cbar[2];
     __shared__ double wsum[32];
     if ((int)blockIdx.x >= *n_items) return;
     const int2 it = items[blockIdx.x];
     const PassArgsT<C> A = args[it.x];
-    ypass_body<MODE, C, 0>(A, it.y, smem_raw, mbar, wsum);
+    ypass_body<MODE, C, 0>(A, it.y, smem_raw, mbar, wsum, cbar);
 }
 
 template <int MODE, typename C, int M>
@@ -1112,11 +1186,12 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
+    __shared__ uint64_t cbar[2];
     __shared__ double wsum[32];
     if ((int)blockIdx.x >= *n_items) return;
     const int2 it = items[blockIdx.x];
     const PassArgsT<C> A = args[it.x];
-    ypass_body<MODE, C, M>(A, it.y, smem_raw, mbar, wsum);
+    ypass_body<MODE, C, M>(A, it.y, smem_raw, mbar, wsum, cbar);
 }
 
 // ------------------------------------------------------------- launchers ---

@@ -43,6 +43,23 @@ def test_fp32_substep_parity(which, mode, so_type):
     assert np.max(np.abs(got - want)) <= 2e-6 * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("which", ["P", "X", "Y"])
+def test_fp32_substeps_on_clustered_tilings(which):
+    """Lines of 320 and 288 points: the default tilings split each line group
+    over a cluster of CTAs, including the substeps that skip the solve."""
+    p = ragged(nx=320, ny=288, xlen=0.05 * 320, ylen=0.05 * 288, dt=0.0005)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=4, phase_noise=0.3) \
+        + inputs.random_state(p["nx"], p["ny"], seed=104, scale=0.05)
+    want = oracle.substep(p, psi, which, IMAG)
+    with gpspin.Solver(p) as s:
+        t = s.tiling(IMAG)
+        assert t["xpass"]["cluster"] > 1 and t["ypass"]["cluster"] > 1
+        s.set_state(psi)
+        s.apply_substep(which, IMAG)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 2e-6 * np.max(np.abs(want))
+
+
 def test_fp32_then_fp64_refinement_matches_oracle_energy():
     """1000 FP32 steps then 1000 FP64 refinement steps versus 2000 FP64 oracle steps
     of the 64 x 64 workload: |dE/E| <= 1e-6 and the density error stated."""
