@@ -976,7 +976,7 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         A.out[2 * plane + o] = xm;
     }
     if constexpr (M > 0) {
-        if (T.S > 1) cluster_wait();  // the cluster's CTAs have read this CTA's carries
+        if (T.S > 1) cluster_wait();  // no neighbour store into this CTA is still in flight
     }
 }
 
@@ -1143,7 +1143,7 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
         }
     }
     if constexpr (M > 0) {
-        if (T.S > 1) cluster_wait();  // the cluster's CTAs have read this CTA's carries
+        if (T.S > 1) cluster_wait();  // no neighbour store into this CTA is still in flight
     }
 }
 
