@@ -251,6 +251,16 @@ int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_ct
  * (complex64, chunk length 16, 24 or 32).  out must hold 8 ints. */
 int gp_tiling_info(gp_handle* h, int mode, int dir, int* out);
 
+/* The default tiling of a pass (dir 0: x-pass, 1: y-pass) for these parameters
+ * and mode, the one a handle starts with, computed on the host without a
+ * device: out[0..7] as gp_tiling_info, then out[8] the fixup length F (rows
+ * a chunk carry reaches above the precision's rounding), out[9] the chunk
+ * stride and out[10] the line-channel stride in shared memory (elements), and
+ * out[11] the extra shared-memory wavefronts that bank conflicts add to one
+ * round of the solve's chunk-parallel accesses (0: none).  out must hold 12 ints.
+ * GP_ERR_ARG or GP_ERR_UNSUPPORTED as gp_create would return them. */
+int gp_plan_tiling(const gp_params* p, int mode, int dir, int* out);
+
 /* Human-readable text for a gp_status. */
 const char* gp_strerror(int status);
 

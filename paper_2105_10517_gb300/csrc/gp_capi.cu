@@ -908,6 +908,31 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
     return st;
 }
 
+int gp_plan_tiling(const gp_params* p, int mode, int dir, int* out)
+{
+    if (!out || (mode != GP_IMAG && mode != GP_REAL) || dir < 0 || dir > 1) return GP_ERR_ARG;
+    int st = validate(p);
+    if (st) return st;
+    const int L = dir == 0 ? p->nx : p->ny, nl = dir == 0 ? p->ny : p->nx;
+    const int kind = p->precision == GP_FP32_MIXED ? TILE_C64_REG : TILE_C128;
+    LineTiling t;
+    if ((st = choose_tiling(L, nl, max_cp(*p, dir, mode), &t, kind))) return st;
+    const int unit = t.single ? 2 : 1, G = t.single ? 8 : (kind == TILE_C128 ? 8 : 16);
+    out[0] = t.S;
+    out[1] = t.R;
+    out[2] = t.m;
+    out[3] = t.Q;
+    out[4] = t.threads;
+    out[5] = (int)t.smem;
+    out[6] = y_blocks(t);
+    out[7] = t.single;
+    out[8] = t.F;
+    out[9] = t.cs;
+    out[10] = t.Lp;
+    out[11] = solve_conflicts(t.cs, t.Lp, 3 * t.R, t.Qc, G, unit);
+    return GP_OK;
+}
+
 int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk)
 {
     if (!h || (mode != GP_IMAG && mode != GP_REAL) || dir < 0 || dir > 1) return GP_ERR_ARG;

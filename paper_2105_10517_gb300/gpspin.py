@@ -33,7 +33,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
            "gp_init_winding", "gp_set_magnetization", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
-           "gp_tiling_info", "gp_set_tiling",
+           "gp_tiling_info", "gp_set_tiling", "gp_plan_tiling",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_strerror"]
 
@@ -156,6 +156,8 @@ def load():
     lib.gp_tiling_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_tiling_info.restype = ctypes.c_int
     lib.gp_set_tiling.argtypes = [vp, ip, ip, ip, ip, ip]
+    lib.gp_plan_tiling.argtypes = [ctypes.POINTER(Params), ip, ip, ctypes.POINTER(ctypes.c_int)]
+    lib.gp_plan_tiling.restype = ctypes.c_int
     lib.gp_set_tiling.restype = ctypes.c_int
     lib.gp_propagate_noalloc.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_longlong, ip, vp]
     lib.gp_propagate_noalloc.restype = ctypes.c_int
@@ -213,6 +215,20 @@ def propagate_noalloc(params, psi_dev_ptr, nsteps, mode=IMAG, stream=None):
     s = ctypes.c_void_p(int(stream)) if stream is not None else None
     _check(load().gp_propagate_noalloc(ctypes.byref(p), ctypes.c_void_p(int(psi_dev_ptr)), int(nsteps), int(mode), s),
            "gp_propagate_noalloc")
+
+
+def plan_tiling(params, mode=IMAG):
+    """Default tilings of the x- and y-pass for these parameters, computed on the
+    host (no device needed)."""
+    p = make_params(params)
+    out = {}
+    for d, name in ((0, "xpass"), (1, "ypass")):
+        v = (ctypes.c_int * 12)()
+        _check(load().gp_plan_tiling(ctypes.byref(p), int(mode), d, v), "gp_plan_tiling")
+        out[name] = dict(cluster=v[0], lines_per_cta=v[1], chunk=v[2], chunks=v[3], threads=v[4], smem=v[5],
+                         ctas=v[6], register_solve=bool(v[7]), fixup=v[8], chunk_stride=v[9], line_stride=v[10],
+                         bank_conflicts=v[11])
+    return out
 
 
 class Solver:
