@@ -22,6 +22,7 @@
  * Readings of what the paper leaves open (each is listed in the design notes):
  *   grid      cell-centred, x_i = -xlen/2 + (i+1/2) dx, psi = 0 outside the box;
  *   splitting Lie order P(dt) -> X(dt) -> Y(dt) -> [imag: renormalise to 1];
+ *             the second-order (Strang) composition is an extension;
  *   P         psi <- exp(-tau' H_loc) psi with H_loc = V + c0 rho + c2 F.Sigma
  *             + R Sigma_x frozen at the start of the substep (c2 and Rabi terms
  *             of Eqs. S.1-S.2), tau' = dt (imaginary time) or i dt (real time);
@@ -414,6 +415,34 @@ int orc_propagate(const orc_params* p, cplx* psi, long long nsteps, int mode)
 /* ---- observables: norms, magnetisation, energy (S.6), chemical potential --- */
 /* Central difference of component c at (j,i) along x (dir 0) or y (dir 1),
  * zero outside the box. */
+/* ---- second-order (Strang) splitting: an extension ----------------------------
+ * The paper names the split-step scheme but not its order; the step above is the
+ * first-order (Lie) reading.  The symmetric composition
+ *   P(dt/2) -> X(dt/2) -> Y(dt) -> X(dt/2) -> P(dt/2) -> [imag: renormalise]
+ * is second order.  Each substep is the one above with its own time step. */
+int orc_step_strang(const orc_params* p, cplx* psi, int mode)
+{
+    orc_params half = *p;
+    half.dt = 0.5 * p->dt;
+    int st;
+    if ((st = orc_substep_p(&half, psi, mode))) return st;
+    if ((st = orc_substep_x(&half, psi, mode))) return st;
+    if ((st = orc_substep_y(p, psi, mode))) return st;
+    if ((st = orc_substep_x(&half, psi, mode))) return st;
+    if ((st = orc_substep_p(&half, psi, mode))) return st;
+    if (mode == ORC_IMAG) return orc_normalize(p, psi);
+    return ORC_OK;
+}
+
+int orc_propagate_strang(const orc_params* p, cplx* psi, long long nsteps, int mode)
+{
+    for (long long s = 0; s < nsteps; ++s) {
+        int st = orc_step_strang(p, psi, mode);
+        if (st) return st;
+    }
+    return ORC_OK;
+}
+
 static cplx dcen(const orc_params* p, const cplx* psi, int c, int j, int i, int dir)
 {
     if (dir == 0) {

@@ -60,6 +60,8 @@ def _load():
             fn.restype = ctypes.c_int
         lib.orc_propagate.argtypes = [cp, dp, ctypes.c_longlong, ctypes.c_int]
         lib.orc_propagate.restype = ctypes.c_int
+        lib.orc_propagate_strang.argtypes = [cp, dp, ctypes.c_longlong, ctypes.c_int]
+        lib.orc_propagate_strang.restype = ctypes.c_int
         lib.orc_normalize_m.argtypes = [cp, dp, ctypes.c_double]
         lib.orc_normalize_m.restype = ctypes.c_int
         lib.orc_step_m.argtypes = [cp, dp, ctypes.c_double]
@@ -124,6 +126,14 @@ def step(p, psi, mode):
 def propagate(p, psi, nsteps, mode):
     a = _buf(psi, p)
     _check(_load().orc_propagate(ctypes.byref(_params(p)), _ptr(a), int(nsteps), int(mode)), "orc_propagate")
+    return a
+
+
+def propagate_strang(p, psi, nsteps, mode):
+    """nsteps second-order (Strang) steps: P(dt/2) X(dt/2) Y(dt) X(dt/2) P(dt/2)."""
+    a = _buf(psi, p)
+    _check(_load().orc_propagate_strang(ctypes.byref(_params(p)), _ptr(a), int(nsteps), int(mode)),
+           "orc_propagate_strang")
     return a
 
 
