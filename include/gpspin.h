@@ -142,6 +142,17 @@ int gp_propagate(gp_handle* h, long long nsteps, int mode);
  * propagates in FP64 from then on.  On a GP_FP64 handle it equals gp_propagate. */
 int gp_refine_fp64(gp_handle* h, long long nsteps, int mode);
 
+/* Splitting of the time step.  GP_SPLIT_LIE (the default) is the first-order
+ * step P(dt) -> X(dt) -> Y(dt) of this library's reading of the paper's
+ * split-step scheme.  GP_SPLIT_STRANG is an extension with no counterpart in the
+ * paper: the second-order symmetric step P(dt/2) -> X(dt/2) -> Y(dt) -> X(dt/2)
+ * -> P(dt/2), followed in imaginary time by the same renormalisation.  Strang
+ * steps run on GP_FP64 handles without the magnetisation constraint
+ * (GP_ERR_UNSUPPORTED otherwise); gp_propagate, gp_refine_fp64 and
+ * gp_propagate_host follow the setting. */
+enum { GP_SPLIT_LIE = 0, GP_SPLIT_STRANG = 1 };
+int gp_set_splitting(gp_handle* h, int split);
+
 /* Magnetisation-constrained imaginary time (both conditions printed below Eq.
  * S.5): with enable != 0, every imaginary-time step ends with psi_c <- sigma_c psi_c
  * such that N = 1 and N_{+1} - N_{-1} = m, with sigma_{+1} sigma_{-1} = sigma_0^2

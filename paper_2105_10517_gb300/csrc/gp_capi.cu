@@ -211,6 +211,9 @@ void free_coef(CoefSet& c)
     cudaFree(c.fy);
     cudaFree(c.fex);
     cudaFree(c.fey);
+    cudaFree(c.cxh);
+    cudaFree(c.exh);
+    cudaFree(c.eyh);
     c = CoefSet{};
 }
 
@@ -257,6 +260,7 @@ int ensure_coef(gp_handle* h, int mode)
         }
     }
     drop_graphs(h);
+    cs.half_valid = false;
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
     const double dx = p.xlen / p.nx, dy = p.ylen / p.ny;
     const double g = gamma_of(p);
@@ -482,8 +486,72 @@ int run_steps(gp_handle* h, int mode, const A& ax, const A& ay, int gy, long lon
 
 namespace {
 
+// Second-order (Strang) steps, complex128: per step
+//   x-pass    P(dt/2) then X(dt/2), with the pending normalisation  (dt/2 tables)
+//   y-pass    Y(dt)                                                 (dt tables)
+//   tail      X(dt/2), then P(dt/2), natural-layout store, partial norms
+//   [imaginary time: norm finalize; the scale is applied by the next x-pass]
+// The x tables of dt/2 are tabulated beside the dt ones; the tiling of the dt
+// tables serves them (their fixups reach fewer rows).
+int ensure_half(gp_handle* h, int mode)
+{
+    CoefSet& cs = h->coef[mode];
+    if (cs.half_valid) return GP_OK;
+    const gp_params& p = h->p;
+    if (!cs.cxh) {
+        bool ok = cudaMalloc(&cs.cxh, sizeof(LineCoef) * 3 * (size_t)p.ny) == cudaSuccess &&
+                  cudaMalloc(&cs.exh, sizeof(double2) * p.nx) == cudaSuccess &&
+                  cudaMalloc(&cs.eyh, sizeof(double2) * p.ny) == cudaSuccess;
+        if (!ok) return GP_ERR_OOM;
+    }
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    const double dx = p.xlen / p.nx, dy = p.ylen / p.ny, hdt = 0.5 * p.dt;
+    LK(launch_coef(cs.cxh, p.ny, 0, mode, dx, p.ylen, dy, hdt, p.omeg, gamma_of(p), eta_of(p), h->flag, h->stream));
+    LK(launch_trap_table(cs.exh, p.nx, p.xlen, p.wx, hdt, mode, h->stream));
+    LK(launch_trap_table(cs.eyh, p.ny, p.ylen, p.wy, hdt, mode, h->stream));
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (flag & 1) return GP_ERR_UNSUPPORTED;
+    cs.half_valid = true;
+    return GP_OK;
+}
+
+int propagate_strang(gp_handle* h, long long nsteps, int mode)
+{
+    if (h->active != GP_FP64 || h->mcon) return GP_ERR_UNSUPPORTED;
+    int st = ensure_coef(h, mode);
+    if (st || (st = ensure_half(h, mode))) return st;
+    const CoefSet& cs = h->coef[mode];
+    const int gx = y_blocks(cs.tx);
+    if (gx > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
+    if (mode == GP_REAL && (st = flush_scale(h))) return st;
+    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+    ax.coef = cs.cxh;
+    ax.ex = cs.exh;
+    ax.ey = cs.eyh;
+    ax.dt = 0.5 * h->p.dt;
+    PassArgs at = ax;  // the tail works in place on psi, with nothing pending
+    at.in = h->psi;
+    at.out = h->psi;
+    at.do_p = 0;
+    at.scale = h->scal + 2;
+    at.partials = mode == GP_IMAG ? h->partials : nullptr;
+    ay.partials = nullptr;
+    for (long long k = 0; k < nsteps; ++k) {
+        LK(launch_xpass(ax, mode, h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
+        LK(launch_xtail(at, mode, h->stream));
+        if (mode == GP_IMAG) LK(launch_finalize_norm(h->partials, gx, cell(h), h->scal, h->flag, h->stream));
+    }
+    if (mode == GP_IMAG) h->scale_pending = true;
+    h->steps += nsteps;
+    return GP_OK;
+}
+
 int propagate_active(gp_handle* h, long long nsteps, int mode)
 {
+    if (h->split == GP_SPLIT_STRANG) return propagate_strang(h, nsteps, mode);
     int st = ensure_coef(h, mode);
     if (st) return st;
     const CoefSet& cs = h->coef[mode];
@@ -610,6 +678,15 @@ int gp_set_params(gp_handle* h, const gp_params* params)
         return GP_ERR_ARG;
     h->p = *params;
     drop_graphs(h);  // the captured launches hold c0, c2, R and dt by value
+    return GP_OK;
+}
+
+int gp_set_splitting(gp_handle* h, int split)
+{
+    if (!h || (split != GP_SPLIT_LIE && split != GP_SPLIT_STRANG)) return GP_ERR_ARG;
+    if (split == GP_SPLIT_STRANG && (h->p.precision != GP_FP64 || h->mcon)) return GP_ERR_UNSUPPORTED;
+    h->split = split;
+    drop_graphs(h);
     return GP_OK;
 }
 
@@ -746,7 +823,7 @@ int gp_propagate_host(gp_handle* h, const double* psi_in, long long nsteps, int 
     const double2* din = device_view(psi_in);
     double2* dout = device_view(psi_out);
     const bool mc = mode == GP_IMAG && h->mcon;
-    if (!din || h->active != GP_FP64 || nsteps == 0) {
+    if (!din || h->active != GP_FP64 || nsteps == 0 || h->split != GP_SPLIT_LIE) {
         int st = gp_set_state(h, psi_in, 0);
         if (st == GP_OK) st = gp_propagate(h, nsteps, mode);
         return st == GP_OK ? gp_get_state(h, psi_out) : st;

@@ -21,6 +21,11 @@ struct CoefSet {
     float2* fey = nullptr;
     LineTiling tx{}, ty{}, ftx{}, fty{};  // single-instance launches (may span 2-CTA clusters)
     LineTiling ux{}, uy{}, fux{}, fuy{};  // unsplit, for batched launches
+    // second-order splitting (complex128): x-pass tables and trap factors of dt/2
+    bool half_valid = false;
+    LineCoef* cxh = nullptr;
+    double2* exh = nullptr;
+    double2* eyh = nullptr;
 };
 
 }  // namespace gpspin
@@ -48,6 +53,7 @@ struct gp_handle {
     long long steps = 0;
     int mcon = 0;              // imaginary time keeps N = 1 and N+ - N- = m_target
     double m_target = 0.0;
+    int split = 0;             // GP_SPLIT_LIE or GP_SPLIT_STRANG
 };
 
 namespace gpspin {

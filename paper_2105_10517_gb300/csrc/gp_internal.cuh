@@ -126,6 +126,8 @@ int launch_coef(LineCoefF* coef, int nlines, int dir, int mode, double h, double
 int launch_trap_table(double2* out, int n, double len, double w, double dt, int mode, cudaStream_t st);
 int launch_trap_table(float2* out, int n, double len, double w, double dt, int mode, cudaStream_t st);
 int launch_xpass(const PassArgs& a, int mode, cudaStream_t st);
+// closing x-pass of a second-order step (solve, U_y, pointwise substep, natural store, partial norms)
+int launch_xtail(const PassArgs& a, int mode, cudaStream_t st);
 int launch_ypass(const PassArgs& a, int mode, cudaStream_t st);
 int launch_xpass(const PassArgsF& a, int mode, cudaStream_t st);
 int launch_ypass(const PassArgsF& a, int mode, cudaStream_t st);

@@ -479,6 +479,21 @@ __device__ __forceinline__ void to_sigma_y(C a, C b, C c, typename RealOf<C>::ty
     z = mkc<C>(rs2 * (a.x + c.x), rs2 * (a.y + c.y));
 }
 
+// psi = U_y phi (the inverse of to_sigma_y without scale):
+//   a = phi_0/sqrt2 + (phi_+ + phi_-)/2,  c = phi_0/sqrt2 - (phi_+ + phi_-)/2,
+//   b = i (phi_+ - phi_-)/sqrt2.
+template <typename C>
+__device__ __forceinline__ void from_sigma_y(C p, C z, C m, C& a, C& b, C& c)
+{
+    typedef typename RealOf<C>::type R;
+    const R rs2 = R(0.70710678118654752440);
+    R sx = R(0.5) * (p.x + m.x), sy = R(0.5) * (p.y + m.y);
+    R zx = rs2 * z.x, zy = rs2 * z.y;
+    a = mkc<C>(zx + sx, zy + sy);
+    c = mkc<C>(zx - sx, zy - sy);
+    b = mkc<C>(-rs2 * (p.y - m.y), rs2 * (p.x - m.x));
+}
+
 // chi = U_x^dagger U_y phi: from Sigma_y channels to Sigma_x channels
 // (Sigma_x eigenvectors (1, sqrt2, 1)/2, (1, 0, -1)/sqrt2, (1, -sqrt2, 1)/2):
 //   chi_{+-} = phi_0/sqrt2 +- (i/2)(phi_+ - phi_-),  chi_0 = (phi_+ + phi_-)/sqrt2.
@@ -844,9 +859,12 @@ struct SPos {
 
 // --------------------------------------------------------------- x-pass ----
 // One CTA of the x-pass: lines cta*R .. cta*R + R - 1 of instance A.
-template <int MODE, typename C, int M>
+// TAIL (second-order splitting, complex128): the solve comes first and the pass
+// ends with psi = U_y phi', the pointwise substep, a natural-layout store and the
+// per-CTA partial norms (wsum: warp sums).
+template <int MODE, typename C, int M, bool TAIL = false>
 __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar,
-                                           uint64_t* cbar)
+                                           uint64_t* cbar, double* wsum = nullptr)
 {
     typedef typename RealOf<C>::type R;
     const LineTiling& T = A.t;
@@ -963,6 +981,41 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     }
     __syncthreads();
     if (A.do_solve) solve_lines<MODE, C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P, cbar, A.err);
+    if constexpr (TAIL) {
+        // psi = U_y phi', then the pointwise substep (constants of this pass),
+        // stored in natural layout; consecutive threads -> consecutive i
+        R acc = R(0);
+        for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+            int r = div_len(e), kl = e - r * Ll, i = k0 + kl, j = line0 + r;
+            const C* src = sa + r * 3 * Lp + spos(kl);
+            C a, b, c;
+            from_sigma_y(src[0], src[Lp], src[2 * Lp], a, b, c);
+            C ev = MODE == 1 ? cmul(A.ex[i], A.ey[j]) : mkc<C>(A.ex[i].x * A.ey[j].x, R(0));
+            R ps;
+            pointwise<MODE>(a, b, c, ev, R(0), k, ps);
+            a = mkc<C>(ps * a.x, ps * a.y);
+            b = mkc<C>(ps * b.x, ps * b.y);
+            c = mkc<C>(ps * c.x, ps * c.y);
+            if (!ok) continue;
+            size_t o = (size_t)j * nx + i;
+            A.out[o] = a;
+            A.out[plane + o] = b;
+            A.out[2 * plane + o] = c;
+            acc += fma(a.x, a.x, a.y * a.y) + fma(b.x, b.x, b.y * b.y) + fma(c.x, c.x, c.y * c.y);
+        }
+        if (A.partials) {
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+            if (lane == 0) wsum[warp] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double t = 0.0;
+                for (int w = 0; w < nw; ++w) t += wsum[w];
+                A.partials[cta] = t;
+            }
+        }
+        return;
+    }
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
     for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, i = k0 + kl, j = line0 + r;
@@ -988,6 +1041,18 @@ __global__ void __launch_bounds__(512) xpass_kernel(PassArgsT<C> A)
     __shared__ uint64_t mbar;
     __shared__ uint64_t cbar[2];
     xpass_body<MODE, C, 0>(A, blockIdx.x, smem_raw, mbar, cbar);
+}
+
+// The closing x-pass of a second-order step (complex128): solve, U_y, pointwise
+// substep, natural-layout store, partial norms.
+template <int MODE>
+__global__ void __launch_bounds__(512) xtail_kernel(PassArgs A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    __shared__ uint64_t cbar[2];
+    __shared__ double wsum[32];
+    xpass_body<MODE, double2, 0, true>(A, blockIdx.x, smem_raw, mbar, cbar, wsum);
 }
 
 // With the register-resident solve of chunk length M (one-array tilings).  The
@@ -1277,6 +1342,11 @@ static int launch_line_pass(const PassArgsT<C>& a, cudaStream_t st)
         return GP_ERR_ARG;  // one line array only with a register-resident solve
     }
     return X ? launch_pass(xpass_kernel<MODE, C>, a, st) : launch_pass(ypass_kernel<MODE, C>, a, st);
+}
+
+int launch_xtail(const PassArgs& a, int mode, cudaStream_t st)
+{
+    return mode == 1 ? launch_pass(xtail_kernel<1>, a, st) : launch_pass(xtail_kernel<0>, a, st);
 }
 
 int launch_xpass(const PassArgs& a, int mode, cudaStream_t st)

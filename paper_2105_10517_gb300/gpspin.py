@@ -23,6 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
 
 IMAG, REAL = 0, 1
+SPLIT_LIE, SPLIT_STRANG = 0, 1
 SO_NONE, SO_RASHBA, SO_DRESSELHAUS = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
 SUB_P, SUB_X, SUB_Y = 0, 1, 2
@@ -32,7 +33,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
-           "gp_init_winding", "gp_set_magnetization", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
+           "gp_init_winding", "gp_set_magnetization", "gp_set_splitting", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
            "gp_tiling_info", "gp_set_tiling", "gp_plan_tiling",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_strerror"]
@@ -143,6 +144,8 @@ def load():
     lib.gp_init_gaussian.argtypes = [vp, dp, ctypes.c_ulonglong, ctypes.c_double]
     lib.gp_init_winding.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int), ctypes.c_ulonglong, ctypes.c_double]
     lib.gp_init_winding.restype = ctypes.c_int
+    lib.gp_set_splitting.argtypes = [vp, ip]
+    lib.gp_set_splitting.restype = ctypes.c_int
     lib.gp_set_magnetization.argtypes = [vp, ip, ctypes.c_double]
     lib.gp_set_magnetization.restype = ctypes.c_int
     lib.gp_propagate.argtypes = [vp, ctypes.c_longlong, ip]
@@ -316,6 +319,10 @@ class Solver:
         f = np.asarray(frac, dtype=np.float64)
         w = (ctypes.c_int * 3)(*[int(v) for v in winding])
         _check(load().gp_init_winding(self._h, _dptr(f), w, int(seed), float(phase_noise)), "gp_init_winding")
+
+    def set_splitting(self, split):
+        """SPLIT_LIE (default) or SPLIT_STRANG (second order, complex128 handles)."""
+        _check(load().gp_set_splitting(self._h, int(split)), "gp_set_splitting")
 
     def set_magnetization(self, m):
         """Keep N = 1 and N+ - N- = m in imaginary time (None: plain renormalisation)."""
