@@ -52,10 +52,10 @@ BYTES_PER_SITE_PASS = 96
 # and valid only while the kernel source is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/*.md)
-    "xpass_kernel<0, double2> vortex512": (16203264 + 256, "fa3e8d9938611767"),
-    "ypass_kernel<0, double2> vortex512": (16174336, "fa3e8d9938611767"),
-    "xpass_kernel_reg<0, float2, 32> precision2048": (105449216 + 57633792, "fa3e8d9938611767"),
-    "ypass_kernel_reg<0, float2, 32> precision2048": (105455104 + 58279424, "fa3e8d9938611767"),
+    "xpass_kernel<0, double2> vortex512": (16202752, "c3e07569008b765c"),
+    "ypass_kernel<0, double2> vortex512": (16175104, "c3e07569008b765c"),
+    "xpass_kernel_reg<0, float2, 32> precision2048": (105452032 + 57134592, "c3e07569008b765c"),
+    "ypass_kernel_reg<0, float2, 32> precision2048": (105460992 + 58541568, "c3e07569008b765c"),
 }
 
 L2_FLUSH_BYTES = 256 << 20
