@@ -45,6 +45,10 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 #   x-pass: P 156 (63 FMA, 27 MUL, 3 ADD) + U_y^dag 16 + Thomas 3 x 22 + U_x^dag U_y 14
 #   y-pass: Thomas 3 x 22 + U_x 16 + |psi|^2 partial sums 12
 FLOPS_PER_SITE = {"xpass": 252, "ypass": 94}
+# Closing x-pass of a second-order (Strang) step, same counting: U_y^dag with the
+# scale 18 + Thomas 3 x 22 + U_y 14 + P 160 (applied after the solve, with its
+# scale) + |psi|^2 partial sums 12.
+FLOPS_XTAIL = 270
 INST_PER_SITE = {"xpass": 155, "ypass": 57}
 # Algorithmic HBM bytes per site and pass: read and write 3 complex128 values.
 BYTES_PER_SITE_PASS = 96
@@ -87,6 +91,10 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-plain", action="store_true", help="serving: skip the one-at-a-time FP64 baseline")
     ap.add_argument("--no-autotune", action="store_true", help="time the default tiling instead of the tuned one")
+    ap.add_argument("--splitting", default="lie", choices=["lie", "strang"],
+                    help="lie: the first-order step (default); strang: the second-order extension (fp64)")
+    ap.add_argument("--magnetization", type=float, default=None,
+                    help="imaginary time with N+ - N- held at this value (the workload without SO and Rabi coupling)")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32"],
                     help="storage precision (default: fp64; precision2048 defaults to fp32)")
     return ap.parse_args()
@@ -204,12 +212,19 @@ def run_ours(args):
     prec = args.precision or ("fp32" if name == "precision2048" else "fp64")
     c, p = workload(name)
     p["precision"] = gpspin.FP32_MIXED if prec == "fp32" else gpspin.FP64
+    if args.magnetization is not None:  # m is conserved only without SO and Rabi coupling
+        for q in (c, p):
+            q.update(so_type=0, gamma=0.0, rabi=0.0)
     mode = c["mode"]
     sites = c["nx"] * c["ny"]
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     s = gpspin.Solver(p, stream=stream.cuda_stream)
     s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+    if args.splitting == "strang":
+        s.set_splitting(gpspin.SPLIT_STRANG)
+    if args.magnetization is not None:
+        s.set_magnetization(args.magnetization)
     tuned_ms = None
     if not args.no_autotune:
         tuned_ms = s.autotune(mode)  # untimed; the state is unchanged
@@ -288,6 +303,9 @@ def run_ours(args):
     td = tiles[dom]
     kname = (f"{dom}_kernel_reg<{mode}, float2, {td['chunk']}>" if td.get("register_solve")
              else f"{dom}_kernel<{mode}, {'float2' if prec == 'fp32' else 'double2'}>")
+    strang = args.splitting == "strang"
+    if strang and dom == "xpass":
+        kname = f"xpass_kernel<{mode}, double2> + xtail_kernel<{mode}> (both x-passes of a second-order step)"
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         hbm = float(peaks["hbm_gbs"])
@@ -296,13 +314,15 @@ def run_ours(args):
     tr = NCU_TRAFFIC.get(f"{kname} {name}")
     traffic = tr[0] if tr and tr[1] == sha_kernels() else None
     if prec == "fp64":
-        achieved = FLOPS_PER_SITE[dom] * sites / (ms_dom / 1e3) / 1e12
+        flops = FLOPS_PER_SITE[dom] + (FLOPS_XTAIL if strang and dom == "xpass" else 0)
+        achieved = flops * sites / (ms_dom / 1e3) / 1e12
         roofline = {
             "bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "peak_source": "derived: 2 FP64 FMA lanes/SM/clk x 152 SMs x 2.07 GHz x 2 flop",
-            "fp64_issue_frac": INST_PER_SITE[dom] * sites / (ms_dom / 1e3) / (FP64_PEAK_TFLOPS / 2 * 1e12),
-            "flops_per_launch": FLOPS_PER_SITE[dom] * sites,
+            "fp64_issue_frac": (None if strang and dom == "xpass" else
+                                INST_PER_SITE[dom] * sites / (ms_dom / 1e3) / (FP64_PEAK_TFLOPS / 2 * 1e12)),
+            "flops_per_launch": flops * sites,
         }
         bytes_site_pass = BYTES_PER_SITE_PASS
     else:
@@ -319,6 +339,11 @@ def run_ours(args):
     roofline["step_hbm_frac_of_measured"] = bytes_site_pass * 2 * sites / (ms_step / 1e3) / 1e9 / hbm
     roofline["hbm_peak_gbs"] = hbm
 
+    # kernels of one step: x-pass, y-pass (+ the closing x-pass of a second-order
+    # step) and in imaginary time the normalisation (two kernels when m is held)
+    launches_per_step = 2 + (1 if strang else 0)
+    if mode == gpspin.IMAG:
+        launches_per_step += 2 if args.magnetization is not None else 1
     out = None
     if rank == 0:
         out = {
@@ -327,9 +352,10 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic (seeded Gaussian + splitmix64 phase noise)",
             "config": dict(config_dict(c, name, prec), tiling="default" if tuned_ms is None else "autotuned",
+                           splitting=args.splitting, magnetization=args.magnetization,
                            tiles=tiles),
             "roofline": roofline, "e2e": e2e,
-            "gpu_launches": 3 * args.steps, "clocks": clocks.summary(), "wall_s_timed_loop": wall,
+            "gpu_launches": launches_per_step * args.steps, "clocks": clocks.summary(), "wall_s_timed_loop": wall,
         }
     s.close()
     if dist:

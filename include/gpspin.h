@@ -171,11 +171,13 @@ int gp_observables(gp_handle* h, gp_obs* out);
 int gp_apply_substep(gp_handle* h, int which, int mode);
 
 /* Timing hook: advances h by ONE step exactly as gp_propagate(h, 1, mode)
- * does, recording CUDA events on the handle's stream between its kernels, and
- * writes the device durations in milliseconds to ms_out[0] (x-pass: pending
- * normalisation, pointwise substep, X sweep), ms_out[1] (y-pass: Y sweep and
- * partial norms), ms_out[2] (normalisation, 0 in real time) and ms_out[3]
- * (the whole step, first event to last).  ms_out must hold 4 floats. */
+ * does (with the handle's splitting and magnetisation settings), recording
+ * CUDA events on the handle's stream between its kernels, and writes the device
+ * durations in milliseconds to ms_out[0] (x-pass: pending normalisation,
+ * pointwise substep, X sweep; with GP_SPLIT_STRANG both x-passes of the step),
+ * ms_out[1] (y-pass: Y sweep and partial norms), ms_out[2] (normalisation, 0 in
+ * real time) and ms_out[3] (the whole step, first event to last).  ms_out must
+ * hold 4 floats. */
 int gp_profile_step(gp_handle* h, int mode, float* ms_out);
 
 /* No-allocation variant of gp_propagate (the paper has no counterpart: it

@@ -517,27 +517,40 @@ int ensure_half(gp_handle* h, int mode)
     return GP_OK;
 }
 
-int propagate_strang(gp_handle* h, long long nsteps, int mode)
+// Pass arguments of a second-order step: x-pass with the dt/2 tables, y-pass
+// (no partials), tail in place on psi with nothing pending (partials in
+// imaginary time).  Returns the tail's CTA count through gx.
+int strang_args(gp_handle* h, int mode, PassArgs* ax, PassArgs* ay, PassArgs* at, int* gx)
 {
     if (h->active != GP_FP64 || h->mcon) return GP_ERR_UNSUPPORTED;
     int st = ensure_coef(h, mode);
     if (st || (st = ensure_half(h, mode))) return st;
     const CoefSet& cs = h->coef[mode];
-    const int gx = y_blocks(cs.tx);
-    if (gx > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
+    *gx = y_blocks(cs.tx);
+    if (*gx > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
     if (mode == GP_REAL && (st = flush_scale(h))) return st;
-    PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
-    ax.coef = cs.cxh;
-    ax.ex = cs.exh;
-    ax.ey = cs.eyh;
-    ax.dt = 0.5 * h->p.dt;
-    PassArgs at = ax;  // the tail works in place on psi, with nothing pending
-    at.in = h->psi;
-    at.out = h->psi;
-    at.do_p = 0;
-    at.scale = h->scal + 2;
-    at.partials = mode == GP_IMAG ? h->partials : nullptr;
-    ay.partials = nullptr;
+    *ax = pass_args(h, cs, 0);
+    *ay = pass_args(h, cs, 1);
+    ax->coef = cs.cxh;
+    ax->ex = cs.exh;
+    ax->ey = cs.eyh;
+    ax->dt = 0.5 * h->p.dt;
+    *at = *ax;
+    at->in = h->psi;
+    at->out = h->psi;
+    at->do_p = 0;
+    at->scale = h->scal + 2;
+    at->partials = mode == GP_IMAG ? h->partials : nullptr;
+    ay->partials = nullptr;
+    return GP_OK;
+}
+
+int propagate_strang(gp_handle* h, long long nsteps, int mode)
+{
+    PassArgs ax, ay, at;
+    int gx = 0;
+    int st = strang_args(h, mode, &ax, &ay, &at, &gx);
+    if (st) return st;
     for (long long k = 0; k < nsteps; ++k) {
         LK(launch_xpass(ax, mode, h->stream));
         LK(launch_ypass(ay, mode, h->stream));
@@ -859,40 +872,79 @@ int gp_propagate_host(gp_handle* h, const double* psi_in, long long nsteps, int 
 int gp_profile_step(gp_handle* h, int mode, float* ms_out)
 {
     if (!h || !ms_out || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
-    int st = ensure_coef(h, mode);
-    if (st) return st;
-    const CoefSet& cs = h->coef[mode];
-    if (mode == GP_REAL && (st = flush_scale(h))) return st;
     for (auto& e : h->ev)
         if (!e) CK(cudaEventCreate(&e));
-    const bool f32 = h->active == GP_FP32_MIXED;
-    const int gy = y_blocks(f32 ? cs.fty : cs.ty);
-    if (gy > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
-    CK(cudaEventRecord(h->ev[0], h->stream));
-    if (f32) {
-        PassArgsF ax = pass_args_f32(h, cs, 0), ay = pass_args_f32(h, cs, 1);
-        if (mode == GP_IMAG) ay.partials = h->partials;
+    float t[4] = {0, 0, 0, 0};
+    if (h->split == GP_SPLIT_STRANG) {
+        // x-pass (dt/2), y-pass, closing x-pass, normalisation
+        PassArgs ax, ay, at;
+        int gx = 0;
+        int st = strang_args(h, mode, &ax, &ay, &at, &gx);
+        if (st) return st;
+        CK(cudaEventRecord(h->ev[0], h->stream));
         LK(launch_xpass(ax, mode, h->stream));
         CK(cudaEventRecord(h->ev[1], h->stream));
         LK(launch_ypass(ay, mode, h->stream));
+        CK(cudaEventRecord(h->ev[2], h->stream));
+        LK(launch_xtail(at, mode, h->stream));
+        CK(cudaEventRecord(h->ev[3], h->stream));
+        if (mode == GP_IMAG) {
+            LK(launch_finalize_norm(h->partials, gx, cell(h), h->scal, h->flag, h->stream));
+            h->scale_pending = true;
+        }
     } else {
-        PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
-        if (mode == GP_IMAG) ay.partials = h->partials;
-        LK(launch_xpass(ax, mode, h->stream));
-        CK(cudaEventRecord(h->ev[1], h->stream));
-        LK(launch_ypass(ay, mode, h->stream));
+        int st = ensure_coef(h, mode);
+        if (st) return st;
+        const CoefSet& cs = h->coef[mode];
+        const bool mc = mode == GP_IMAG && h->mcon;
+        if (mc && (gamma_of(h->p) != 0.0 || h->p.rabi != 0.0)) return GP_ERR_ARG;
+        if ((mode == GP_REAL || mc) && (st = flush_scale(h))) return st;
+        const bool f32 = h->active == GP_FP32_MIXED;
+        const int gy = y_blocks(f32 ? cs.fty : cs.ty);
+        if (gy * (mc ? 3 : 1) > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
+        CK(cudaEventRecord(h->ev[0], h->stream));
+        if (f32) {
+            PassArgsF ax = pass_args_f32(h, cs, 0), ay = pass_args_f32(h, cs, 1);
+            if (mode == GP_IMAG) ay.partials = h->partials;
+            ay.mcomp = mc;
+            LK(launch_xpass(ax, mode, h->stream));
+            CK(cudaEventRecord(h->ev[1], h->stream));
+            LK(launch_ypass(ay, mode, h->stream));
+            CK(cudaEventRecord(h->ev[2], h->stream));
+            CK(cudaEventRecord(h->ev[3], h->stream));
+            if (mc) {
+                LK(launch_finalize_m(h->partials, gy, cell(h), h->m_target, h->scal + 3, h->flag, h->stream));
+                LK(apply_sigma(h, ay));
+            }
+        } else {
+            PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
+            if (mode == GP_IMAG) ay.partials = h->partials;
+            ay.mcomp = mc;
+            LK(launch_xpass(ax, mode, h->stream));
+            CK(cudaEventRecord(h->ev[1], h->stream));
+            LK(launch_ypass(ay, mode, h->stream));
+            CK(cudaEventRecord(h->ev[2], h->stream));
+            CK(cudaEventRecord(h->ev[3], h->stream));
+            if (mc) {
+                LK(launch_finalize_m(h->partials, gy, cell(h), h->m_target, h->scal + 3, h->flag, h->stream));
+                LK(apply_sigma(h, ay));
+            }
+        }
+        if (mode == GP_IMAG && !mc) {
+            LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
+            h->scale_pending = true;
+        }
     }
-    CK(cudaEventRecord(h->ev[2], h->stream));
-    if (mode == GP_IMAG) {
-        LK(launch_finalize_norm(h->partials, gy, cell(h), h->scal, h->flag, h->stream));
-        h->scale_pending = true;
-    }
-    CK(cudaEventRecord(h->ev[3], h->stream));
-    CK(cudaEventSynchronize(h->ev[3]));
-    CK(cudaEventElapsedTime(&ms_out[0], h->ev[0], h->ev[1]));
-    CK(cudaEventElapsedTime(&ms_out[1], h->ev[1], h->ev[2]));
-    CK(cudaEventElapsedTime(&ms_out[2], h->ev[2], h->ev[3]));
-    CK(cudaEventElapsedTime(&ms_out[3], h->ev[0], h->ev[3]));
+    CK(cudaEventRecord(h->ev[4], h->stream));
+    CK(cudaEventSynchronize(h->ev[4]));
+    CK(cudaEventElapsedTime(&t[0], h->ev[0], h->ev[1]));
+    CK(cudaEventElapsedTime(&t[1], h->ev[1], h->ev[2]));
+    CK(cudaEventElapsedTime(&t[2], h->ev[2], h->ev[3]));
+    CK(cudaEventElapsedTime(&t[3], h->ev[3], h->ev[4]));
+    ms_out[0] = t[0] + t[2];  // x-passes (the closing one of a second-order step included)
+    ms_out[1] = t[1];
+    ms_out[2] = t[3];
+    CK(cudaEventElapsedTime(&ms_out[3], h->ev[0], h->ev[4]));
     h->steps += 1;
     return GP_OK;
 }

@@ -47,7 +47,7 @@ struct gp_handle {
     double* obs_out = nullptr; // [8]
     int* flag = nullptr;       // bit0 coefficient convergence, bit1 norm, bit2 observables, bit3 copy timeout
     gpspin::CoefSet coef[2];   // per mode
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // gp_profile_step
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // gp_profile_step
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [precision][mode]
     bool scale_pending = false;
     long long steps = 0;
