@@ -113,6 +113,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err)
 // for every thread of the cluster to have arrived.
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
+// Arrive without release ordering: for the start of a pass, whose only job is
+// to publish mbarrier initialisations that their own fence.mbarrier_init
+// (release, cluster scope) already orders.
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+}
 
 // Point-to-point carries between neighbouring CTAs of a cluster: the producer
 // stores the value into the neighbour's shared memory and arrives on the
@@ -887,7 +894,7 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
                 mbar_init(&cbar[0], 3 * nl);
                 mbar_init(&cbar[1], 3 * nl);
             }
-            cluster_arrive();
+            cluster_arrive_relaxed();
         }
     }
     // pending normalisation, loaded before the staging wait (complex64 pass)
@@ -1124,7 +1131,7 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
                 mbar_init(&cbar[0], 3 * nl);
                 mbar_init(&cbar[1], 3 * nl);
             }
-            cluster_arrive();
+            cluster_arrive_relaxed();
         }
     }
     // with one line array (M > 0) the chunks are staged in place and need no copy
