@@ -56,10 +56,10 @@ BYTES_PER_SITE_PASS = 96
 # and valid only while the kernel source is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/*.md)
-    "xpass_kernel<0, double2> vortex512": (16202752, "c3e07569008b765c"),
-    "ypass_kernel<0, double2> vortex512": (16175104, "c3e07569008b765c"),
-    "xpass_kernel_reg<0, float2, 32> precision2048": (105452032 + 57134592, "c3e07569008b765c"),
-    "ypass_kernel_reg<0, float2, 32> precision2048": (105460992 + 58541568, "c3e07569008b765c"),
+    "xpass_kernel<0, double2> vortex512": (16210432 + 512, "eb250b4a7edbda2f"),
+    "ypass_kernel<0, double2> vortex512": (16175104 + 256, "eb250b4a7edbda2f"),
+    "xpass_kernel_reg<0, float2, 32> precision2048": (105435136 + 56283136, "eb250b4a7edbda2f"),
+    "ypass_kernel_reg<0, float2, 32> precision2048": (105467648 + 57590528, "eb250b4a7edbda2f"),
 }
 
 L2_FLUSH_BYTES = 256 << 20
