@@ -111,7 +111,8 @@ int gp_get_state(gp_handle* h, double* psi_out);
  * gp_get_state(h, psi_out), and the handle holds the new state afterwards.
  * psi_in and psi_out are complex128 psi[3][ny][nx] host buffers owned by the
  * caller (they may be the same buffer); the call returns once psi_out is
- * written.  On a GP_FP64 handle, when the device can address the buffers
+ * written.  On a GP_FP64 handle with the first-order splitting (the default),
+ * when the device can address the buffers
  * (pinned memory, or pageable memory on systems where the GPU reads host page
  * tables, such as NVLink-C2C hosts) and they are 16-byte aligned, the first
  * x-pass reads psi_in directly, so the host-to-device transfer overlaps the
