@@ -20,7 +20,6 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-import numpy as np  # noqa: E402
 
 import oracle  # noqa: E402
 from paper_2105_10517_gb300 import inputs  # noqa: E402
