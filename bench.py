@@ -52,10 +52,10 @@ FLOPS_XTAIL = 270
 INST_PER_SITE = {"xpass": 155, "ypass": 57}
 # Algorithmic HBM bytes per site and pass: read and write 3 complex128 values.
 BYTES_PER_SITE_PASS = 96
-# DRAM traffic of one launch from an ncu capture (profiles/), keyed by kernel
-# and valid only while the kernel source is unchanged (sha256 prefix).
+# DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture of that kernel), keyed by kernel and workload and valid only
+# while the kernel source is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/*.md)
     "xpass_kernel<0, double2> vortex512": (16210432 + 512, "eb250b4a7edbda2f"),
     "ypass_kernel<0, double2> vortex512": (16175104 + 256, "eb250b4a7edbda2f"),
     "xpass_kernel_reg<0, float2, 32> precision2048": (105435136 + 56283136, "eb250b4a7edbda2f"),

@@ -187,18 +187,22 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out);
  * no-allocation rule -- and therefore cannot create a gp_handle).
  *   params  problem statement as for gp_create; nx and ny must be <= 256
  *           (otherwise GP_ERR_TOO_LARGE, before any device work).
- *   psi_dev DEVICE pointer owned by the caller: psi[3][ny][nx] complex128,
+ *   psi_dev DEVICE pointer owned by the caller, 16-byte aligned (otherwise
+ *           GP_ERR_ARG, before any device work): psi[3][ny][nx] complex128,
  *           advanced in place by nsteps steps in mode GP_IMAG or GP_REAL;
  *           in imaginary time it is returned normalised to 1.
  *   cuda_stream  a cudaStream_t (NULL: the legacy default stream).
+ * Returns GP_ERR_UNSUPPORTED for parameters outside the tabulated solver's
+ * range, GP_ERR_TIMEOUT if a bounded device-side wait gave up (psi is then
+ * unreliable) and GP_ERR_NONFINITE if a norm became NaN or Inf.
  * The call allocates nothing: its intermediate, coefficient tables, partial
  * sums and scalars live in fixed device arrays of the library (about 8.6 MB,
  * held on every device that loads the library until the process exits).  The
  * first call on a device looks up their addresses (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  All calls share these
- * arrays: two calls whose device work overlaps (other streams, other host
- * threads) race and corrupt each other's results.  Synchronous with respect to
- * cuda_stream. */
+ * make that first call before any stream capture; a lookup that failed is
+ * tried again by the next call.  All calls share these arrays: two calls whose
+ * device work overlaps (other streams, other host threads) race and corrupt
+ * each other's results.  Synchronous with respect to cuda_stream. */
 int gp_propagate_noalloc(const gp_params* params, double* psi_dev, long long nsteps, int mode, void* cuda_stream);
 
 /* ---- Served, batched solves --------------------------------------------------

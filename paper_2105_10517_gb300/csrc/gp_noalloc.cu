@@ -47,17 +47,21 @@ struct Scratch {
 };
 
 constexpr int kMaxDevices = 64;
-std::once_flag g_once[kMaxDevices];
+std::mutex g_setup_mutex;
 Scratch g_scratch[kMaxDevices];
-int g_setup_status[kMaxDevices];
+bool g_ready[kMaxDevices];
 
 int lookup(void** p, const void* sym, const char* what)
 {
     return report_cuda(cudaGetSymbolAddress(p, sym), what);
 }
 
-void setup(int dev)
+// Looks the addresses up for the current device.  A failed lookup is not
+// remembered: the next call on that device tries again.
+int setup(int dev)
 {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (g_ready[dev]) return GP_OK;
     Scratch s{};
     int bad = 0;
     bad |= lookup((void**)&s.work, g_work, "cudaGetSymbolAddress(g_work)");
@@ -68,8 +72,10 @@ void setup(int dev)
     bad |= lookup((void**)&s.partials, g_partials, "cudaGetSymbolAddress(g_partials)");
     bad |= lookup((void**)&s.scale, g_scale, "cudaGetSymbolAddress(g_scale)");
     bad |= lookup((void**)&s.flag, &g_flag, "cudaGetSymbolAddress(g_flag)");
+    if (bad) return GP_ERR_CUDA;
     g_scratch[dev] = s;
-    g_setup_status[dev] = bad ? GP_ERR_CUDA : GP_OK;
+    g_ready[dev] = true;
+    return GP_OK;
 }
 
 #define NK(x)                                                  \
@@ -92,14 +98,15 @@ extern "C" int gp_propagate_noalloc(const gp_params* params, double* psi_dev, lo
     int st = validate(params);
     if (st) return st;
     if (!psi_dev || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
+    // the passes move psi as 16-byte complex128 values
+    if (reinterpret_cast<uintptr_t>(psi_dev) % 16 != 0) return GP_ERR_ARG;
     const gp_params& p = *params;
     if (p.nx > kMaxLine || p.ny > kMaxLine) return GP_ERR_TOO_LARGE;
     if (nsteps == 0) return GP_OK;
     int dev = 0;
     NK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return GP_ERR_CUDA;
-    std::call_once(g_once[dev], setup, dev);
-    if (g_setup_status[dev] != GP_OK) return g_setup_status[dev];
+    if ((st = setup(dev))) return st;
     const Scratch& S = g_scratch[dev];
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
@@ -151,7 +158,7 @@ extern "C" int gp_propagate_noalloc(const gp_params* params, double* psi_dev, lo
     ax.y0 = ay.y0 = -0.5 * p.ylen + 0.5 * dy;
     ax.wx = ay.wx = p.wx;
     ax.wy = ay.wy = p.wy;
-    ax.t.bulk = ((size_t)p.nx * sizeof(double2)) % 16 == 0 && (reinterpret_cast<uintptr_t>(psi_dev) % 16) == 0;
+    ax.t.bulk = ((size_t)p.nx * sizeof(double2)) % 16 == 0;
     ay.t.bulk = ((size_t)p.ny * sizeof(double2)) % 16 == 0;
     const double da = dx * dy;
     const int gy = (ty.nlines + ty.R - 1) / ty.R * ty.S;
@@ -166,5 +173,9 @@ extern "C" int gp_propagate_noalloc(const gp_params* params, double* psi_dev, lo
                                                S.scale, stream));
     NK(cudaMemcpyAsync(&flag, S.flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
     NK(cudaStreamSynchronize(stream));
-    return (flag & 2) ? GP_ERR_NONFINITE : GP_OK;
+    // the same order as gp_propagate: a bulk-copy wait that gave up (bit 8)
+    // makes psi unreliable, then a non-finite norm (bit 2)
+    if (flag & 8) return GP_ERR_TIMEOUT;
+    if (flag & 2) return GP_ERR_NONFINITE;
+    return GP_OK;
 }

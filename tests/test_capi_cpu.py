@@ -54,3 +54,16 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gpspin, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         gpspin.load()
+
+
+def test_noalloc_rejects_before_any_device_work(lib):
+    """gp_propagate_noalloc turns a misaligned psi pointer and a grid beyond its
+    fixed scratch into errors before it touches the device (there is no device
+    here: any CUDA call would fail with GP_ERR_CUDA instead)."""
+    lib = gpspin.load()
+    p = gpspin.make_params(dict(nx=64, ny=64, xlen=8.0, ylen=8.0, dt=0.01))
+    misaligned = ctypes.c_void_p(0x1000 + 8)
+    assert lib.gp_propagate_noalloc(ctypes.byref(p), misaligned, 1, 0, None) == 1
+    big = gpspin.make_params(dict(nx=257, ny=16, xlen=8.0, ylen=8.0, dt=0.01))
+    assert lib.gp_propagate_noalloc(ctypes.byref(big), ctypes.c_void_p(0x1000), 1, 0, None) == 6
+    assert lib.gp_propagate_noalloc(ctypes.byref(p), None, 1, 0, None) == 1

@@ -31,11 +31,17 @@ def test_noalloc_matches_propagate_twice(mode, shape):
     dev = torch.from_numpy(psi0.copy()).to("cuda")
     with gpspin.Solver(p) as ref:
         ref.set_state(psi0)
-        for _ in range(2):
+        for call in range(2):
             ref.propagate(15, mode)
             want = ref.get_state()
             torch.cuda.synchronize()
+            # after the first call (module loaded, scratch addresses looked up) a
+            # call must not take any device memory
+            free_before = torch.cuda.mem_get_info()[0]
             gpspin.propagate_noalloc(p, dev.data_ptr(), 15, mode, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            if call == 1:
+                assert torch.cuda.mem_get_info()[0] >= free_before
             got = dev.cpu().numpy()
             assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
 
