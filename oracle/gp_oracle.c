@@ -41,6 +41,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 
@@ -71,6 +74,26 @@ static double trap_v(const orc_params* p, double x, double y)
 }
 static int so_eta(const orc_params* p) { return p->so_type == 1 ? 1 : (p->so_type == 2 ? -1 : 0); }
 static double so_gamma(const orc_params* p) { return p->so_type == 0 ? 0.0 : p->gamma; }
+
+/* ---- threads ---------------------------------------------------------------
+ * The substeps work on independent grid lines (rows for P and X, columns for Y),
+ * the way the paper's program spreads them over OpenMP threads.  Each line's
+ * arithmetic is the same whichever thread runs it, so every thread count gives
+ * bitwise identical results; the sums (norms, observables) stay sequential. */
+static int g_threads = 1;
+
+/* Sets the number of threads the substeps use (n >= 1); returns the number in
+ * effect (1 when the library was built without OpenMP). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
 
 static int check_params(const orc_params* p)
 {
@@ -196,6 +219,9 @@ int orc_substep_p(const orc_params* p, cplx* psi, int mode)
     int st = check_params(p);
     if (st) return st;
     cplx tau = mode == ORC_REAL ? I * p->dt : p->dt;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+#endif
     for (int j = 0; j < p->ny; ++j)
         for (int i = 0; i < p->nx; ++i) {
             cplx v[3] = { PSI(psi, p, 0, j, i), PSI(psi, p, 1, j, i), PSI(psi, p, 2, j, i) };
@@ -287,16 +313,30 @@ int orc_substep_x(const orc_params* p, cplx* psi, int mode)
     cplx sx[9], sy[9], sz[9];
     spin_matrices(sx, sy, sz);
     cplx tau = mode == ORC_REAL ? I * 0.5 * p->dt : 0.5 * p->dt;
-    cplx* work = malloc(sizeof(cplx) * 15 * (size_t)p->nx);
-    if (!work) return ORC_ENOMEM;
     size_t plane = (size_t)p->nx * p->ny;
-    for (int j = 0; j < p->ny && !st; ++j) {
-        double y = grid_y(p, j);
-        cplx k[9];
-        for (int q = 0; q < 9; ++q) k[q] = (q % 4 == 0 ? -I * p->omeg * y : 0.0) + I * so_gamma(p) * sy[q];
-        st = cn_line(&PSI(psi, p, 0, j, 0), 1, plane, p->nx, grid_dx(p), k, tau, work);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(g_threads)
+#endif
+    {
+        int lst = ORC_OK;
+        cplx* work = malloc(sizeof(cplx) * 15 * (size_t)p->nx);
+        if (!work) lst = ORC_ENOMEM;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int j = 0; j < p->ny; ++j) {
+            if (lst) continue;
+            double y = grid_y(p, j);
+            cplx k[9];
+            for (int q = 0; q < 9; ++q) k[q] = (q % 4 == 0 ? -I * p->omeg * y : 0.0) + I * so_gamma(p) * sy[q];
+            lst = cn_line(&PSI(psi, p, 0, j, 0), 1, plane, p->nx, grid_dx(p), k, tau, work);
+        }
+        free(work);
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        if (lst && !st) st = lst;
     }
-    free(work);
     return st;
 }
 
@@ -308,17 +348,31 @@ int orc_substep_y(const orc_params* p, cplx* psi, int mode)
     cplx sx[9], sy[9], sz[9];
     spin_matrices(sx, sy, sz);
     cplx tau = mode == ORC_REAL ? I * 0.5 * p->dt : 0.5 * p->dt;
-    cplx* work = malloc(sizeof(cplx) * 15 * (size_t)p->ny);
-    if (!work) return ORC_ENOMEM;
     size_t plane = (size_t)p->nx * p->ny;
-    for (int i = 0; i < p->nx && !st; ++i) {
-        double x = grid_x(p, i);
-        cplx k[9];
-        for (int q = 0; q < 9; ++q)
-            k[q] = (q % 4 == 0 ? I * p->omeg * x : 0.0) - I * so_eta(p) * so_gamma(p) * sx[q];
-        st = cn_line(&PSI(psi, p, 0, 0, i), (size_t)p->nx, plane, p->ny, grid_dy(p), k, tau, work);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(g_threads)
+#endif
+    {
+        int lst = ORC_OK;
+        cplx* work = malloc(sizeof(cplx) * 15 * (size_t)p->ny);
+        if (!work) lst = ORC_ENOMEM;
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (int i = 0; i < p->nx; ++i) {
+            if (lst) continue;
+            double x = grid_x(p, i);
+            cplx k[9];
+            for (int q = 0; q < 9; ++q)
+                k[q] = (q % 4 == 0 ? I * p->omeg * x : 0.0) - I * so_eta(p) * so_gamma(p) * sx[q];
+            lst = cn_line(&PSI(psi, p, 0, 0, i), (size_t)p->nx, plane, p->ny, grid_dy(p), k, tau, work);
+        }
+        free(work);
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        if (lst && !st) st = lst;
     }
-    free(work);
     return st;
 }
 

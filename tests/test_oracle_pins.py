@@ -319,3 +319,75 @@ def test_constrained_imaginary_time_keeps_m_and_lowers_energy():
     # SO or Rabi coupling does not conserve m: the constrained flow is rejected there
     with pytest.raises(oracle.OracleError):
         oracle.propagate_m(dict(p, rabi=0.1), psi, 1, 0.25)
+
+
+# ---------------------------------------------------------------------------
+# The composition of one step (reading of the paper's split-step scheme, program
+# summary "Solution method", and of the normalisation condition below Eq. S.5):
+# P(dt), then X(dt), then Y(dt), then in imaginary time the rescaling to N = 1.
+# Built here from scipy's expm per site and the dense CN solves of tests/dense.py,
+# in that order; swapping X and Y, or normalising before Y, or applying P last
+# must each miss, so the pin fixes the order and not only the pieces.
+def _dense_p(p, psi, mode):
+    v = dense.trap(p)
+    tau = p["dt"] * (1j if mode == REAL else 1.0)
+    out = np.empty_like(psi)
+    for j in range(p["ny"]):
+        for i in range(p["nx"]):
+            s = psi[:, j, i]
+            rho = np.sum(np.abs(s) ** 2)
+            f = [np.real(np.vdot(s, m @ s)) for m in (dense.SX, dense.SY, dense.SZ)]
+            h = (v[j, i] + p["c0"] * rho) * np.eye(3) + p["c2"] * (
+                f[0] * dense.SX + f[1] * dense.SY + f[2] * dense.SZ) + p["rabi"] * dense.SX
+            out[:, j, i] = scipy.linalg.expm(-tau * h) @ s
+    return out
+
+
+def _dense_norm(p, psi):
+    da = (p["xlen"] / p["nx"]) * (p["ylen"] / p["ny"])
+    return psi / math.sqrt(da * np.sum(np.abs(psi) ** 2))
+
+
+def _dense_step(p, psi, mode, order="PXYN"):
+    for s in order:
+        if s == "P":
+            psi = _dense_p(p, psi, mode)
+        elif s == "X":
+            psi = dense.cn(dense.a_x(p), psi, p["dt"], mode)
+        elif s == "Y":
+            psi = dense.cn(dense.a_y(p), psi, p["dt"], mode)
+        elif s == "N" and mode == IMAG:
+            psi = _dense_norm(p, psi)
+    return psi
+
+
+@pytest.mark.parametrize("mode", [IMAG, REAL])
+@pytest.mark.parametrize("so_type", [1, 2])
+def test_step_is_p_then_x_then_y_then_normalise(mode, so_type):
+    p = tiny(so_type=so_type, c0=30.0, c2=-12.0, rabi=1.5, dt=0.04)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=61, phase_noise=0.5) \
+        + inputs.random_state(p["nx"], p["ny"], seed=62, scale=0.1)
+    got = oracle.step(p, psi, mode)
+    want = _dense_step(p, psi, mode)
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(got - want)) <= 1e-13 * scale
+    # negative controls: each plausible misordering misses by far more than rounding
+    wrong = ["PYXN", "XPYN", "PXNY" if mode == IMAG else "XYP"]
+    for order in wrong:
+        assert np.max(np.abs(_dense_step(p, psi, mode, order) - want)) > 1e-6 * scale, order
+
+
+# The oracle spreads independent lines over threads (the paper's program runs its
+# line loops under OpenMP); the result must not depend on the thread count.
+@pytest.mark.parametrize("mode", [IMAG, REAL])
+def test_oracle_threads_give_bitwise_identical_steps(mode):
+    p = tiny(nx=40, ny=33, xlen=8.0, ylen=6.6, so_type=2)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=63, phase_noise=0.3)
+    try:
+        oracle.set_threads(1)
+        one = oracle.propagate(p, psi, 5, mode)
+        n = oracle.set_threads(4)
+        many = oracle.propagate(p, psi, 5, mode)
+    finally:
+        oracle.set_threads(1)
+    assert np.array_equal(one, many), n
