@@ -1,12 +1,15 @@
 #!/usr/bin/env python3
 """Benchmark of the split-step Crank-Nicolson step (one JSON line on rank 0).
 
-A bench step is one time step of the whole hot path: pending normalisation,
-pointwise substep P, X sweep, Y sweep and the imaginary-time renormalisation,
-on the 512 x 512 imaginary-time vortex-lattice workload ([-16,16]^2, dt = 1e-3,
-c0 = 500, c2 = -10, Omega = 0.8, Rashba gamma = 1, R = 0) from its seeded
-Gaussian initial state.  The metric is site-steps per second (one grid point
-advanced one full step, all three components).
+A bench step is one time step of the whole hot path.  The default workload is
+the 1024 x 1024 real-time run ([-20,20]^2, dt = 5e-4, c0 = 800, c2 = 15,
+Dresselhaus gamma = 0.75, R = 0.5): the seeded Gaussian initial state is first
+relaxed by imaginary-time steps at Omega = 0.6 (untimed), Omega is then quenched
+to 0.9 (the tables are rebuilt) and the real-time steps -- pointwise substep P,
+X sweep, Y sweep -- are timed in FP64.  The metric is site-steps per second (one
+grid point advanced one full step, all three components).  The same line carries
+the 2048 x 2048 FP32-storage step (the HBM-bound form) and the 512 x 512 FP64
+imaginary-time step as extra keys.
 
   python bench.py [--gpus N --steps K --warmup W]   the CUDA path (C ABI)
   python bench.py --impl reference ...              the FP64 CPU oracle
@@ -31,7 +34,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Msite-steps/s & %HBM peak; served solves/s, p50/p99 vs plain FP64 at ΔE/E≤1e-6"
 UNIT = "Msite-steps/s"
-WORKLOAD = "vortex512"
+WORKLOAD = "quench1024"
+# Workloads whose timed steps follow an untimed preparation: imaginary-time steps
+# from the seeded Gaussian state, then new parameters (the Omega quench).
+PREP = {"quench1024": dict(imag_steps=4000, quench=dict(omeg=0.9))}
+# Extra lines measured after the main one (N = 1 only): workload, storage, steps.
+EXTRAS = (("precision2048", "fp32", 1500), ("vortex512", "fp64", 1500))
 
 # Roofline of the FP64 path: it is bound by FP64 issue, not HBM.  GB300 retires
 # 2 FP64 FMA lanes per SM per clock (measured 1.2 TFLOP/s, rate independent of
@@ -45,11 +53,20 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 #   x-pass: P 156 (63 FMA, 27 MUL, 3 ADD) + U_y^dag 16 + Thomas 3 x 22 + U_x^dag U_y 14
 #   y-pass: Thomas 3 x 22 + U_x 16 + |psi|^2 partial sums 12
 FLOPS_PER_SITE = {"xpass": 252, "ypass": 94}
+INST_PER_SITE = {"xpass": 155, "ypass": 57}
+# Real time, same counting: the Thomas pivots are complex (26 flops, 14
+# instructions per channel point: forward cmul + cfnma, back cfnma, 2w - phi), and
+# P applies exp(-i dt (V + c0 rho)) as a complex phase (cis series, trap factor
+# product, three complex products) and has no partial norms.
+#   x-pass: P 192 (77 FMA, 35 MUL, 3 ADD; 115 instructions) + U_y^dag 16 (12)
+#           + Thomas 3 x 26 (3 x 14) + U_x^dag U_y 14 (14)
+#   y-pass: Thomas 3 x 26 (3 x 14) + U_x 16 (12)
+FLOPS_PER_SITE_REAL = {"xpass": 300, "ypass": 94}
+INST_PER_SITE_REAL = {"xpass": 183, "ypass": 54}
 # Closing x-pass of a second-order (Strang) step, same counting: U_y^dag with the
 # scale 18 + Thomas 3 x 22 + U_y 14 + P 160 (applied after the solve, with its
 # scale) + |psi|^2 partial sums 12.
 FLOPS_XTAIL = 270
-INST_PER_SITE = {"xpass": 155, "ypass": 57}
 # Algorithmic HBM bytes per site and pass: read and write 3 complex128 values.
 BYTES_PER_SITE_PASS = 96
 # DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum from
@@ -76,13 +93,16 @@ def sha_kernels():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=200)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="seconds of oracle work per CPU-baseline leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, help="vortex512 (default), quench1024 or precision2048")
+    ap.add_argument("--no-extras", action="store_true", help="skip the extra workload lines")
+    ap.add_argument("--workload", default=WORKLOAD, help="quench1024 (default), vortex512, precision2048, small64")
+    ap.add_argument("--prep-steps", type=int, default=None,
+                    help="imaginary-time steps before the timed real-time steps (quench1024; default 4000)")
     ap.add_argument("--serve", action="store_true",
                     help="serving benchmark: the seeded request trace through the batched server and one at a time")
     ap.add_argument("--requests", type=int, default=256)
@@ -101,24 +121,34 @@ def parse():
 
 
 def workload(name=WORKLOAD):
+    """(run-control dict, physics of the timed steps): for a prepared workload the
+    physics after the quench."""
     from paper_2105_10517_gb300 import inputs
     c = dict(inputs.CONFIGS[name])
-    return c, inputs.physics(c)
+    p = inputs.physics(c)
+    if name in PREP:
+        p.update(PREP[name]["quench"])
+    return c, p
 
 
-def config_dict(c, name=WORKLOAD, precision="fp64"):
-    so = {0: "no SO", 1: "Rashba", 2: "Dresselhaus"}[c["so_type"]]
+def config_dict(c, p, name=WORKLOAD, precision="fp64", prep_steps=None):
+    so = {0: "no SO", 1: "Rashba", 2: "Dresselhaus"}[p["so_type"]]
     mode = "imaginary" if c["mode"] == 0 else "real"
     half = c["xlen"] / 2
-    return {
+    om = f"Omega={c['omeg']}->{p['omeg']} (quench)" if p["omeg"] != c["omeg"] else f"Omega={p['omeg']}"
+    out = {
         "workload": f"{name}: {c['nx']}x{c['ny']} {mode}-time, [-{half:g},{half:g}]^2, dt={c['dt']}, "
-                    f"c0={c['c0']}, c2={c['c2']}, Omega={c['omeg']}, {so} gamma={c['gamma']}, R={c['rabi']}",
+                    f"c0={p['c0']}, c2={p['c2']}, {om}, {so} gamma={p['gamma']}, R={p['rabi']}",
         "nx": c["nx"], "ny": c["ny"], "dt": c["dt"], "mode": mode, "storage": precision,
-        "step": "one split-step CN time step: normalise, P, X sweep, Y sweep" + (", norm" if mode == "imaginary"
-                                                                                  else ""),
+        "step": "one split-step CN time step: " + ("normalise, " if mode == "imaginary" else "")
+                + "P, X sweep, Y sweep" + (", norm" if mode == "imaginary" else ""),
         "l2": "flushed by a 256 MiB device write before every timed step",
         "parallelism": "replicas",
     }
+    if prep_steps:
+        out["prep"] = (f"{prep_steps} untimed imaginary-time steps at Omega={c['omeg']} from the seeded Gaussian "
+                       f"state, then the quench")
+    return out
 
 
 # ----------------------------------------------------------- rank logic ----
@@ -194,6 +224,113 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ our arm -----
+def kernel_name(dom, mode, prec, tiles, strang):
+    td = tiles[dom]
+    if strang and dom == "xpass":
+        return f"xpass_kernel<{mode}, double2> + xtail_kernel<{mode}> (both x-passes of a second-order step)"
+    if td.get("register_solve"):
+        return f"{dom}_kernel_reg<{mode}, float2, {td['chunk']}>"
+    return f"{dom}_kernel<{mode}, {'float2' if prec == 'fp32' else 'double2'}>"
+
+
+def roofline_of(name, prec, mode, sites, ms_x, ms_y, ms_n, ms_step, tiles, strang):
+    """Roofline of the dominant kernel: FP64 ALU for complex128 storage (bound by
+    FP64 issue on GB300), HBM for complex64 storage."""
+    dom = "xpass" if ms_x >= ms_y else "ypass"
+    ms_dom = ms_x if dom == "xpass" else ms_y
+    kname = kernel_name(dom, mode, prec, tiles, strang)
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm = float(peaks["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        hbm, peaks = 6800.0, None
+    tr = NCU_TRAFFIC.get(f"{kname} {name}")
+    traffic = tr[0] if tr and tr[1] == sha_kernels() else None
+    if prec == "fp64":
+        fl = FLOPS_PER_SITE_REAL if mode == 1 else FLOPS_PER_SITE
+        ins = INST_PER_SITE_REAL if mode == 1 else INST_PER_SITE
+        flops = fl[dom] + (FLOPS_XTAIL if strang and dom == "xpass" else 0)
+        achieved = flops * sites / (ms_dom / 1e3) / 1e12
+        r = {
+            "bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": "derived: 2 FP64 FMA lanes/SM/clk x 152 SMs x 2.07 GHz x 2 flop",
+            "fp64_issue_frac": (None if strang and dom == "xpass" else
+                                ins[dom] * sites / (ms_dom / 1e3) / (FP64_PEAK_TFLOPS / 2 * 1e12)),
+            "flops_per_site": flops, "flops_per_launch": flops * sites,
+        }
+        bytes_site_pass = BYTES_PER_SITE_PASS
+    else:
+        bytes_site_pass = BYTES_PER_SITE_PASS // 2
+        achieved = bytes_site_pass * sites / (ms_dom / 1e3) / 1e9
+        r = {
+            "bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm,
+            "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback",
+            "bytes_per_site": bytes_site_pass, "bytes_per_launch": bytes_site_pass * sites,
+        }
+    r["traffic"] = traffic
+    r["kernel_ms"] = {"xpass": ms_x, "ypass": ms_y, "normalise": ms_n}
+    r["step_hbm_frac_of_measured"] = bytes_site_pass * 2 * sites / (ms_step / 1e3) / 1e9 / hbm
+    r["hbm_peak_gbs"] = hbm
+    return r
+
+
+def prepare(name, prec, stream, args, main=True):
+    """A Solver on the workload's initial state, prepared and tuned (untimed)."""
+    from paper_2105_10517_gb300 import gpspin
+    c, p = workload(name)
+    p["precision"] = gpspin.FP32_MIXED if prec == "fp32" else gpspin.FP64
+    if main and args.magnetization is not None:  # m is conserved only without SO and Rabi coupling
+        p.update(so_type=0, gamma=0.0, rabi=0.0)
+    mode = c["mode"]
+    prep_steps = None
+    if name in PREP:
+        prep_steps = PREP[name]["imag_steps"] if args.prep_steps is None else args.prep_steps
+        s = gpspin.Solver(dict(p, omeg=c["omeg"]), stream=stream)
+        s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+        if prep_steps:
+            s.propagate(prep_steps, gpspin.IMAG)
+        s.set_params(p)  # the quench: tables are rebuilt for the timed physics
+    else:
+        s = gpspin.Solver(p, stream=stream)
+        s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
+    if main and args.splitting == "strang":
+        s.set_splitting(gpspin.SPLIT_STRANG)
+    if main and args.magnetization is not None:
+        s.set_magnetization(args.magnetization)
+    tuned_ms = None if args.no_autotune else s.autotune(mode)  # the state is unchanged
+    return s, c, p, mode, prep_steps, tuned_ms
+
+
+def timed_steps(s, mode, steps, warmup, stream, flush, barrier, clocks=None):
+    """Per-step device times (x-pass, y-pass, normalisation, step) of `steps`
+    steps after `warmup` untimed ones, the L2 flushed before every step."""
+    import torch
+    for _ in range(max(3, warmup)):
+        s.profile_step(mode)
+    if clocks:
+        clocks.start()
+    barrier()
+    t0 = time.perf_counter()
+    per = []
+    torch.cuda.nvtx.range_push("bench_timed")  # ncu --nvtx --nvtx-include "bench_timed/"
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        per.append(s.profile_step(mode))
+    torch.cuda.nvtx.range_pop()
+    barrier()
+    wall = time.perf_counter() - t0
+    if clocks:
+        # keep the GPU busy until the sampler has seen the load a few times
+        t1 = time.perf_counter()
+        while len(clocks.lines) < 5 and time.perf_counter() - t1 < 3.0:
+            s.propagate(20, mode)
+        clocks.stop()
+    return per, wall
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -210,27 +347,8 @@ def run_ours(args):
     gpspin.build()
     name = args.workload
     prec = args.precision or ("fp32" if name == "precision2048" else "fp64")
-    c, p = workload(name)
-    p["precision"] = gpspin.FP32_MIXED if prec == "fp32" else gpspin.FP64
-    if args.magnetization is not None:  # m is conserved only without SO and Rabi coupling
-        for q in (c, p):
-            q.update(so_type=0, gamma=0.0, rabi=0.0)
-    mode = c["mode"]
-    sites = c["nx"] * c["ny"]
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    s = gpspin.Solver(p, stream=stream.cuda_stream)
-    s.init_gaussian((0.25, 0.5, 0.25), seed=c["seed"], phase_noise=1e-3)
-    if args.splitting == "strang":
-        s.set_splitting(gpspin.SPLIT_STRANG)
-    if args.magnetization is not None:
-        s.set_magnetization(args.magnetization)
-    tuned_ms = None
-    if not args.no_autotune:
-        tuned_ms = s.autotune(mode)  # untimed; the state is unchanged
-    tiles = s.tiling(mode)
-    for _ in range(max(3, args.warmup)):
-        s.profile_step(mode)
 
     def barrier():
         torch.cuda.synchronize()
@@ -238,39 +356,27 @@ def run_ours(args):
             dist.barrier()
             torch.cuda.synchronize()
 
+    s, c, p, mode, prep_steps, tuned_ms = prepare(name, prec, stream.cuda_stream, args)
+    sites = c["nx"] * c["ny"]
+    tiles = s.tiling(mode)
     clocks = ClockSampler(local)
-    clocks.start()
-    barrier()
-    t0 = time.perf_counter()
-    per = []
-    torch.cuda.nvtx.range_push("bench_timed")  # ncu --nvtx --nvtx-include "bench_timed/"
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        per.append(s.profile_step(mode))
-    torch.cuda.nvtx.range_pop()
-    barrier()
-    wall = time.perf_counter() - t0
-    # keep the GPU busy until the sampler has seen the load a few times
-    t1 = time.perf_counter()
-    while len(clocks.lines) < 5 and time.perf_counter() - t1 < 3.0:
-        s.propagate(20, mode)
-    clocks.stop()
-
+    per, wall = timed_steps(s, mode, args.steps, args.warmup, stream, flush, barrier, clocks)
     ms_x = statistics.fmean(q[0] for q in per)
     ms_y = statistics.fmean(q[1] for q in per)
     ms_n = statistics.fmean(q[2] for q in per)
     ms_step = statistics.fmean(q[3] for q in per)
-    total_ms = ms_step * args.steps
-    t_max = max_over_ranks(total_ms, dist, "cuda")
+    t_max = max_over_ranks(ms_step * args.steps, dist, "cuda")
     value = whole_job_value(world, sites, args.steps, t_max)
+    strang = args.splitting == "strang"
+    roofline = roofline_of(name, prec, mode, sites, ms_x, ms_y, ms_n, ms_step, tiles, strang)
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers (the timed
+    # physics, starting from the prepared state)
     e2e = None
     if args.e2e_steps > 0:
-        psi0 = inputs.gaussian_state(c["nx"], c["ny"], p["xlen"], p["ylen"], seed=c["seed"])
-        hin = torch.from_numpy(psi0).pin_memory()
+        hin = torch.from_numpy(s.get_state()).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
+
         def one_call(a, b):
             s.propagate_host(a, 1, mode, out=b)
 
@@ -297,53 +403,36 @@ def run_ours(args):
                "path": "gp_propagate_host(pinned in, 1 step, pinned out) per step",
                "three_calls_value": timed(three_calls),
                "three_calls_path": "gp_set_state + gp_propagate(1) + gp_get_state per step"}
-
-    dom = "xpass" if ms_x >= ms_y else "ypass"
-    ms_dom = ms_x if dom == "xpass" else ms_y
-    td = tiles[dom]
-    kname = (f"{dom}_kernel_reg<{mode}, float2, {td['chunk']}>" if td.get("register_solve")
-             else f"{dom}_kernel<{mode}, {'float2' if prec == 'fp32' else 'double2'}>")
-    strang = args.splitting == "strang"
-    if strang and dom == "xpass":
-        kname = f"xpass_kernel<{mode}, double2> + xtail_kernel<{mode}> (both x-passes of a second-order step)"
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm = float(peaks["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        hbm, peaks = 6800.0, None
-    tr = NCU_TRAFFIC.get(f"{kname} {name}")
-    traffic = tr[0] if tr and tr[1] == sha_kernels() else None
-    if prec == "fp64":
-        flops = FLOPS_PER_SITE[dom] + (FLOPS_XTAIL if strang and dom == "xpass" else 0)
-        achieved = flops * sites / (ms_dom / 1e3) / 1e12
-        roofline = {
-            "bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_source": "derived: 2 FP64 FMA lanes/SM/clk x 152 SMs x 2.07 GHz x 2 flop",
-            "fp64_issue_frac": (None if strang and dom == "xpass" else
-                                INST_PER_SITE[dom] * sites / (ms_dom / 1e3) / (FP64_PEAK_TFLOPS / 2 * 1e12)),
-            "flops_per_launch": flops * sites,
-        }
-        bytes_site_pass = BYTES_PER_SITE_PASS
-    else:
-        bytes_site_pass = BYTES_PER_SITE_PASS // 2
-        achieved = bytes_site_pass * sites / (ms_dom / 1e3) / 1e9
-        roofline = {
-            "bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm,
-            "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "of fallback",
-            "bytes_per_launch": bytes_site_pass * sites,
-        }
-    roofline["traffic"] = traffic
-    roofline["kernel_ms"] = {"xpass": ms_x, "ypass": ms_y, "normalise": ms_n}
-    roofline["step_hbm_frac_of_measured"] = bytes_site_pass * 2 * sites / (ms_step / 1e3) / 1e9 / hbm
-    roofline["hbm_peak_gbs"] = hbm
+    s.close()
 
     # kernels of one step: x-pass, y-pass (+ the closing x-pass of a second-order
     # step) and in imaginary time the normalisation (two kernels when m is held)
     launches_per_step = 2 + (1 if strang else 0)
     if mode == gpspin.IMAG:
         launches_per_step += 2 if args.magnetization is not None else 1
+
+    # extra lines: other workloads, each timed the same way (N = 1 only)
+    extras = {}
+    if world == 1 and not args.no_extras:
+        for xname, xprec, xsteps in EXTRAS:
+            if xname == name and xprec == prec:
+                continue
+            xs, xc, xp, xmode, xprep, _ = prepare(xname, xprec, stream.cuda_stream, args, main=False)
+            xsites = xc["nx"] * xc["ny"]
+            xtiles = xs.tiling(xmode)
+            xclocks = ClockSampler(local)
+            xper, _ = timed_steps(xs, xmode, xsteps, args.warmup, stream, flush, barrier, xclocks)
+            xs.close()
+            f = [statistics.fmean(q[k] for q in xper) for k in range(4)]
+            extras[f"{xname}_{xprec}"] = {
+                "value": xsites / (f[3] / 1e3) / 1e6, "unit": UNIT, "ms_per_step": f[3], "steps": xsteps,
+                "dtype": "f32" if xprec == "fp32" else "f64",
+                "config": dict(config_dict(xc, xp, xname, xprec, xprep), tiles=xtiles),
+                "roofline": roofline_of(xname, xprec, xmode, xsites, f[0], f[1], f[2], f[3], xtiles, False),
+                "gpu_launches": (2 + (1 if xmode == gpspin.IMAG else 0)) * xsteps,
+                "clocks": xclocks.summary(),
+            }
+
     out = None
     if rank == 0:
         out = {
@@ -351,13 +440,14 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic (seeded Gaussian + splitmix64 phase noise)",
-            "config": dict(config_dict(c, name, prec), tiling="default" if tuned_ms is None else "autotuned",
-                           splitting=args.splitting, magnetization=args.magnetization,
-                           tiles=tiles),
+            "config": dict(config_dict(c, p, name, prec, prep_steps),
+                           tiling="default" if tuned_ms is None else "autotuned",
+                           splitting=args.splitting, magnetization=args.magnetization, tiles=tiles),
             "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps, "clocks": clocks.summary(), "wall_s_timed_loop": wall,
         }
-    s.close()
+        if extras:
+            out["extra_workloads"] = extras
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -382,12 +472,31 @@ def oracle_rate(p, nx, steps, seconds=None, mode=0):
     return nx * nx * done / el, done, el
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(p, seconds, mode=0):
-    rate, done, el = oracle_rate(p, p["nx"], None, seconds, mode)
+    """The oracle as it stands on the full workload: one leg single-threaded, one
+    leg with its line loops on every host core (the paper's program is OpenMP
+    over grid lines).  The all-cores leg is the reported value."""
+    import oracle
     kind = "imaginary" if mode == 0 else "real"
-    return {"value": rate / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} {kind}-time steps of the full {p['nx']}x{p['ny']} workload "
-                      f"({el:.1f} s, single-threaded C oracle)"}
+    legs = []
+    for want in (1, host_cores()):
+        n = oracle.set_threads(want)
+        rate, done, el = oracle_rate(p, p["nx"], None, seconds, mode)
+        legs.append({"value": rate / 1e6, "unit": UNIT, "cores": n,
+                     "sample": f"{done} {kind}-time steps of the full {p['nx']}x{p['ny']} workload ({el:.1f} s)"})
+        if n == 1 and want > 1:
+            break
+    main = legs[-1]
+    return {"value": main["value"], "unit": UNIT, "cores": main["cores"], "kind": "oracle",
+            "sample": main["sample"] + f", C oracle with OpenMP over lines on {main['cores']} host threads",
+            "legs": legs}
 
 
 def run_reference(args):
@@ -395,6 +504,7 @@ def run_reference(args):
         return None
     import oracle
     oracle.build()
+    cores = oracle.set_threads(host_cores())
     c, p = workload(args.workload)
     # calibrate: size the sample grid so that warmup + steps take about two minutes
     r, _, _ = oracle_rate(p, 64, 3, mode=c["mode"])
@@ -404,13 +514,14 @@ def run_reference(args):
     rate, done, el = oracle_rate(p, n, args.steps, mode=c["mode"])
     value = rate / 1e6
     sample = (f"{n}x{n} grid with the {p['nx']}x{p['ny']} workload's dx, dt and physics, "
-              f"{done} timed steps after {args.warmup} warm-up steps ({el:.1f} s)")
+              f"{done} timed steps after {args.warmup} warm-up steps ({el:.1f} s), "
+              f"C oracle with OpenMP over lines on {cores} host threads")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian)",
-        "config": config_dict(c, args.workload),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": config_dict(c, p, args.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }

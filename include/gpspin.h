@@ -181,6 +181,14 @@ int gp_apply_substep(gp_handle* h, int which, int mode);
  * hold 4 floats. */
 int gp_profile_step(gp_handle* h, int mode, float* ms_out);
 
+/* Test hook for failure detection: runs the bounded device-side wait that the
+ * line passes use for their bulk copies, on the handle's stream, against an
+ * mbarrier that no copy targets and no thread arrives on, so it gives up after
+ * `polls` polls (1 .. 65536) with nothing in flight.  Returns GP_ERR_TIMEOUT,
+ * exactly as gp_propagate does when a copy wait of a pass gives up; the state and
+ * the handle are untouched and stay usable. */
+int gp_check_wait_timeout(gp_handle* h, int polls);
+
 /* No-allocation variant of gp_propagate (the paper has no counterpart: it
  * exists for callers that must not allocate device memory -- e.g. a plugin
  * whose host application owns the GPU memory pool, or a real-time loop under a

@@ -82,12 +82,12 @@ static double so_gamma(const orc_params* p) { return p->so_type == 0 ? 0.0 : p->
  * bitwise identical results; the sums (norms, observables) stay sequential. */
 static int g_threads = 1;
 
-/* Sets the number of threads the substeps use (n >= 1); returns the number in
- * effect (1 when the library was built without OpenMP). */
+/* Sets the number of threads the substeps use (n >= 1; n <= 0 only queries);
+ * returns the number in effect (1 when the library was built without OpenMP). */
 int orc_set_threads(int n)
 {
 #ifdef _OPENMP
-    g_threads = n < 1 ? 1 : n;
+    if (n > 0) g_threads = n;
 #else
     (void)n;
     g_threads = 1;

@@ -84,7 +84,7 @@ def _load():
 
 def set_threads(n):
     """Threads over grid lines in the substeps (results are bitwise the same for
-    every count); returns the count in effect."""
+    every count); returns the count in effect.  n <= 0 only queries it."""
     return int(_load().orc_set_threads(int(n)))
 
 

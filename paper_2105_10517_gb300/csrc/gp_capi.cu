@@ -1123,6 +1123,14 @@ int gp_apply_substep(gp_handle* h, int which, int mode)
     return sync_status(h);
 }
 
+int gp_check_wait_timeout(gp_handle* h, int polls)
+{
+    if (!h || polls < 1 || polls > (1 << 16)) return GP_ERR_ARG;
+    CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
+    LK(launch_wait_probe(polls, h->flag, h->stream));
+    return check_flags(h);
+}
+
 int gp_observables(gp_handle* h, gp_obs* out)
 {
     if (!h || !out) return GP_ERR_ARG;

@@ -142,6 +142,8 @@ int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_
                          size_t smem, int mode, cudaStream_t st, int m_reg = 0);
 int launch_ypass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
                          size_t smem, int mode, cudaStream_t st, int m_reg = 0);
+// the bounded mbarrier wait of the passes on a barrier nothing arrives on
+int launch_wait_probe(int tries, int* err, cudaStream_t st);
 // launchers (gp_reduce.cu)
 int launch_norm(const double2* psi, size_t n, double* partials, int nblk, double da, double* scale, int* flag,
                 cudaStream_t st);

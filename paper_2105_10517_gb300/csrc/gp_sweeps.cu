@@ -91,22 +91,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity)
 }
 
 // Bounded wait on phase 0 of the barrier.  Returns true (for the whole CTA) once
-// the copies have landed; if any thread gives up after kWaitTries polls, the
+// the copies have landed; if any thread gives up after `tries` polls, the
 // CTA sets bit 8 of *err, waits once more (again bounded) so that no copy is
 // still writing its shared memory, and returns false.
 constexpr int kWaitTries = 1 << 22;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err, int tries = kWaitTries)
 {
     bool ok = false;
-    for (int it = 0; it < kWaitTries && !ok; ++it) ok = mbar_try_wait(m, 0);
+    for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, 0);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && err) atomicOr(err, 8);
-        for (int it = 0; it < kWaitTries && !ok; ++it) ok = mbar_try_wait(m, 0);
+        for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, 0);
         __syncthreads();
         return false;
     }
     return true;
+}
+
+// Check of the give-up path above: the same bounded wait on an mbarrier that no
+// copy targets and no thread arrives on, so its phase never completes and
+// nothing is in flight when the CTA gives up after `tries` polls (bit 8 set).
+__global__ void wait_probe_kernel(int tries, int* err)
+{
+    __shared__ uint64_t mbar;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    mbar_wait_bounded(&mbar, err, tries);
+}
+
+int launch_wait_probe(int tries, int* err, cudaStream_t st)
+{
+    wait_probe_kernel<<<1, 32, 0, st>>>(tries, err);
+    return report_cuda(cudaGetLastError(), "wait_probe_kernel launch");
 }
 
 // Cluster barrier in two halves: an arrive that does not wait and a later wait

@@ -34,7 +34,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
            "gp_init_winding", "gp_set_magnetization", "gp_set_splitting", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
-           "gp_tiling_info", "gp_set_tiling", "gp_plan_tiling",
+           "gp_tiling_info", "gp_set_tiling", "gp_plan_tiling", "gp_check_wait_timeout",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_strerror"]
 
@@ -162,6 +162,8 @@ def load():
     lib.gp_plan_tiling.argtypes = [ctypes.POINTER(Params), ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_plan_tiling.restype = ctypes.c_int
     lib.gp_set_tiling.restype = ctypes.c_int
+    lib.gp_check_wait_timeout.argtypes = [vp, ip]
+    lib.gp_check_wait_timeout.restype = ctypes.c_int
     lib.gp_propagate_noalloc.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_longlong, ip, vp]
     lib.gp_propagate_noalloc.restype = ctypes.c_int
     lib.gp_request_bytes.argtypes = [ctypes.POINTER(Params), ip]
@@ -366,6 +368,11 @@ class Solver:
             out[name] = dict(cluster=v[0], lines_per_cta=v[1], chunk=v[2], chunks=v[3], threads=v[4], smem=v[5],
                              ctas=v[6], register_solve=bool(v[7]))
         return out
+
+    def check_wait_timeout(self, polls=64):
+        """Run the passes' bounded device wait on a barrier nothing completes
+        (raises GPError with GP_ERR_TIMEOUT, as a propagate whose copy wait gave up)."""
+        _check(load().gp_check_wait_timeout(self._h, int(polls)), "gp_check_wait_timeout")
 
     def observables(self):
         o = Obs()

@@ -383,11 +383,12 @@ def test_step_is_p_then_x_then_y_then_normalise(mode, so_type):
 def test_oracle_threads_give_bitwise_identical_steps(mode):
     p = tiny(nx=40, ny=33, xlen=8.0, ylen=6.6, so_type=2)
     psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=63, phase_noise=0.3)
+    keep = oracle.set_threads(0)
     try:
         oracle.set_threads(1)
         one = oracle.propagate(p, psi, 5, mode)
         n = oracle.set_threads(4)
         many = oracle.propagate(p, psi, 5, mode)
     finally:
-        oracle.set_threads(1)
+        oracle.set_threads(keep)
     assert np.array_equal(one, many), n
