@@ -34,7 +34,8 @@ typedef enum {
     GP_ERR_NONFINITE = 4, /* a reduction met NaN/Inf in psi; the state is kept as is      */
     GP_ERR_UNSUPPORTED = 5,/* parameters outside what the tabulated solver supports       */
     GP_ERR_TOO_LARGE = 6, /* grid larger than the fixed scratch of gp_propagate_noalloc    */
-    GP_ERR_TIMEOUT = 7    /* a bounded device-side wait gave up; the state is unreliable   */
+    GP_ERR_TIMEOUT = 7,   /* a bounded device-side wait gave up; the state is unreliable   */
+    GP_ERR_QUEUE_FULL = 8 /* gp_batch_submit: the batch's queue limit is reached            */
 } gp_status;
 
 typedef enum { GP_IMAG = 0, GP_REAL = 1 } gp_mode;
@@ -224,7 +225,14 @@ int gp_propagate_noalloc(const gp_params* params, double* psi_dev, long long nst
  * freeing their memory for the next admission.  A solve's result is the same
  * alone and in any mix (bitwise: each CTA runs the single-instance arithmetic). */
 typedef struct gp_batch gp_batch;
-typedef enum { GP_REQ_QUEUED = 0, GP_REQ_RUNNING = 1, GP_REQ_DONE = 2, GP_REQ_FAILED = 3, GP_REQ_UNKNOWN = 4 } gp_req_state;
+typedef enum {
+    GP_REQ_QUEUED = 0,
+    GP_REQ_RUNNING = 1,
+    GP_REQ_DONE = 2,
+    GP_REQ_FAILED = 3,   /* gp_batch_error gives the status that failed it */
+    GP_REQ_UNKNOWN = 4,
+    GP_REQ_CANCELLED = 5
+} gp_req_state;
 typedef enum { GP_POLICY_FP64 = 0, GP_POLICY_FP32_REFINE = 1 } gp_policy;
 
 typedef struct {
@@ -242,8 +250,20 @@ typedef struct {
 size_t gp_request_bytes(const gp_params* params, int policy);
 int gp_batch_create(size_t max_device_bytes, int check_every, void* cuda_stream, gp_batch** out);
 void gp_batch_destroy(gp_batch* b);
-/* Queues a solve (params.precision is set from the policy); *id_out identifies it. */
+/* Queues a solve (params.precision is set from the policy); *id_out identifies it.
+ * GP_ERR_QUEUE_FULL if the queue limit (gp_batch_set_queue_limit) is reached. */
 int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req, long long* id_out);
+/* Limits the number of queued (not yet admitted) requests; 0: no limit. */
+int gp_batch_set_queue_limit(gp_batch* b, int max_queued);
+/* Cancels a queued or running solve between ticks: a queued one leaves the
+ * queue, a running one releases its device memory at once (the next tick can
+ * admit into it).  Its state becomes GP_REQ_CANCELLED; finished solves are left
+ * as they are.  GP_ERR_ARG for an unknown id. */
+int gp_batch_cancel(gp_batch* b, long long id);
+/* The status that failed a GP_REQ_FAILED solve (GP_ERR_OOM when its memory could
+ * not be had with no solve running to free any, GP_ERR_NONFINITE, ...), GP_OK
+ * otherwise; GP_ERR_ARG for an unknown id. */
+int gp_batch_error(gp_batch* b, long long id);
 /* One tick: admit, advance every running solve by check_every steps, check, retire, admit. */
 int gp_batch_step(gp_batch* b, int* n_running, int* n_queued);
 /* State (gp_req_state), steps taken and last observables of a solve; psi_out
@@ -286,6 +306,26 @@ int gp_tiling_info(gp_handle* h, int mode, int dir, int* out);
  * round of the solve's chunk-parallel accesses (0: none).  out must hold 12 ints.
  * GP_ERR_ARG or GP_ERR_UNSUPPORTED as gp_create would return them. */
 int gp_plan_tiling(const gp_params* p, int mode, int dir, int* out);
+
+/* Failure injection for tests of out-of-memory handling: the after-th device
+ * allocation of the library from now on (0: the next one) fails as if the
+ * device were full, once; after < 0 disarms.  Process-wide. */
+void gp_inject_alloc_failure(long long after);
+
+/* Checkpoints (the paper resumes runs from converged wave functions; this is
+ * the exact form of that).  A checkpoint holds the handle's parameters, step
+ * count, storage precision, pending imaginary-time scale and stored state, in
+ * host byte order; restoring it into a handle of the same grid and precision
+ * and propagating gives bitwise the results of the uninterrupted run (same
+ * library build and tilings).  gp_checkpoint_bytes is the buffer size that
+ * gp_checkpoint_save needs (0 for NULL); the caller owns the buffer and may
+ * write it to a file.  gp_checkpoint_load returns GP_ERR_ARG, changing nothing,
+ * for a buffer that is not a checkpoint of this format or whose grid or
+ * precision differ from the handle's; it adopts the checkpoint's physical
+ * parameters and step count. */
+size_t gp_checkpoint_bytes(gp_handle* h);
+int gp_checkpoint_save(gp_handle* h, void* buf, size_t size);
+int gp_checkpoint_load(gp_handle* h, const void* buf, size_t size);
 
 /* Human-readable text for a gp_status. */
 const char* gp_strerror(int status);

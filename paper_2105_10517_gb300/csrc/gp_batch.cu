@@ -31,7 +31,7 @@ struct DevBuf {
         p = nullptr;
         cap = 0;
         size_t c = std::max<size_t>(n, 64);
-        if (cudaMalloc(&p, c * sizeof(T)) != cudaSuccess) return GP_ERR_OOM;
+        if (!dalloc(&p, c * sizeof(T))) return GP_ERR_OOM;
         cap = c;
         return GP_OK;
     }
@@ -54,6 +54,7 @@ struct Request {
     bool have_e = false;
     double e_last = 0;
     gp_obs obs{};
+    int error = GP_OK;        // status that failed the request
     std::vector<double> psi;  // result, complex128, after completion
 };
 
@@ -134,6 +135,7 @@ struct gp_batch {
     Group<float2> g32;
     int* counts = nullptr;  // device: kGroupCounts per precision group (complex128, complex64)
     int* flag = nullptr;
+    int max_queued = 0;     // 0: no limit on queued requests
 };
 
 namespace {
@@ -223,6 +225,13 @@ void retire(gp_batch* b, Request& q, int state)
     q.state = state;
 }
 
+int running_count(const gp_batch* b)
+{
+    int n = 0;
+    for (const auto& kv : b->reqs) n += kv.second.state == GP_REQ_RUNNING;
+    return n;
+}
+
 // Admits queued requests in arrival order while their footprint fits.
 int admit(gp_batch* b)
 {
@@ -230,21 +239,28 @@ int admit(gp_batch* b)
         Request& q = b->reqs[b->queue.front()];
         if (q.bytes > b->max_bytes) {  // can never fit
             q.state = GP_REQ_FAILED;
+            q.error = GP_ERR_OOM;
             b->queue.pop_front();
             continue;
         }
         if (b->used_bytes + q.bytes > b->max_bytes) break;
         gp_handle* h = nullptr;
         int st = gp_create(&q.p, b->stream, &h);
-        if (st == GP_ERR_OOM) break;  // the device is fuller than the accounting: wait for retirements
+        // The device is fuller than the accounting: wait for retirements while
+        // solves are running; with none running nothing will free memory, so the
+        // request fails (out of memory) instead of waiting forever.
+        if (st == GP_ERR_OOM && running_count(b) > 0) break;
         b->queue.pop_front();
         if (st != GP_OK) {
             q.state = GP_REQ_FAILED;
+            q.error = st;
             continue;
         }
-        if (gp_init_gaussian(h, q.r.frac, q.r.seed, q.r.phase_noise) != GP_OK || ensure_coef(h, GP_IMAG) != GP_OK) {
+        if ((st = gp_init_gaussian(h, q.r.frac, q.r.seed, q.r.phase_noise)) != GP_OK ||
+            (st = ensure_coef(h, GP_IMAG)) != GP_OK) {
             gp_destroy(h);
             q.state = GP_REQ_FAILED;
+            q.error = st;
             continue;
         }
         q.h = h;
@@ -283,7 +299,7 @@ int gp_batch_create(size_t max_device_bytes, int check_every, void* cuda_stream,
         }
         b->own_stream = true;
     }
-    if (cudaMalloc(&b->counts, 2 * kGroupCounts * sizeof(int)) != cudaSuccess || cudaMalloc(&b->flag, sizeof(int)) != cudaSuccess ||
+    if (!dalloc(&b->counts, 2 * kGroupCounts * sizeof(int)) || !dalloc(&b->flag, sizeof(int)) ||
         cudaMemsetAsync(b->flag, 0, sizeof(int), b->stream) != cudaSuccess) {
         gp_batch_destroy(b);
         return GP_ERR_OOM;
@@ -314,6 +330,7 @@ int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req,
     if (req->policy != GP_POLICY_FP64 && req->policy != GP_POLICY_FP32_REFINE) return GP_ERR_ARG;
     if (!(req->tol > 0) || req->cap <= 0 || req->refine_steps < 0 || !std::isfinite(req->phase_noise))
         return GP_ERR_ARG;
+    if (b->max_queued > 0 && (int)b->queue.size() >= b->max_queued) return GP_ERR_QUEUE_FULL;
     Request q;
     q.id = b->next_id++;
     q.p = *params;
@@ -367,6 +384,7 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
         int ost = gp_observables(q->h, &o);
         q->obs = o;
         if (ost != GP_OK) {
+            q->error = ost;
             retire(b, *q, GP_REQ_FAILED);
             continue;
         }
@@ -377,7 +395,8 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
             // FP32 phase: hand over to FP64 once the energy has settled to the FP32
             // level, and in any case early enough for a final FP64 refinement block
             if (de <= q->r.tol32 * std::fabs(o.energy) || q->steps + q->r.refine_steps >= q->r.cap) {
-                if (gp_refine_fp64(q->h, 0, GP_IMAG) != GP_OK) {
+                if ((ost = gp_refine_fp64(q->h, 0, GP_IMAG)) != GP_OK) {
+                    q->error = ost;
                     retire(b, *q, GP_REQ_FAILED);
                     continue;
                 }
@@ -397,6 +416,42 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
     return st;
 }
 
+int gp_batch_set_queue_limit(gp_batch* b, int max_queued)
+{
+    if (!b || max_queued < 0) return GP_ERR_ARG;
+    b->max_queued = max_queued;
+    return GP_OK;
+}
+
+int gp_batch_cancel(gp_batch* b, long long id)
+{
+    if (!b) return GP_ERR_ARG;
+    auto it = b->reqs.find(id);
+    if (it == b->reqs.end()) return GP_ERR_ARG;
+    Request& q = it->second;
+    if (q.state == GP_REQ_QUEUED) {
+        b->queue.erase(std::remove(b->queue.begin(), b->queue.end(), id), b->queue.end());
+        q.state = GP_REQ_CANCELLED;
+    } else if (q.state == GP_REQ_RUNNING) {
+        // between ticks no work of the solve is in flight: its memory is freed now
+        // and the next gp_batch_step can admit into it
+        if (q.h) {
+            gp_destroy(q.h);
+            q.h = nullptr;
+            b->used_bytes -= q.bytes;
+        }
+        q.state = GP_REQ_CANCELLED;
+    }
+    return GP_OK;
+}
+
+int gp_batch_error(gp_batch* b, long long id)
+{
+    if (!b) return GP_ERR_ARG;
+    auto it = b->reqs.find(id);
+    return it == b->reqs.end() ? GP_ERR_ARG : it->second.error;
+}
+
 int gp_batch_poll(gp_batch* b, long long id, int* state, long long* steps, gp_obs* obs, double* psi_out, int release)
 {
     if (!b) return GP_ERR_ARG;
@@ -411,7 +466,8 @@ int gp_batch_poll(gp_batch* b, long long id, int* state, long long* steps, gp_ob
     if (obs) *obs = q.obs;
     if (q.state == GP_REQ_DONE && psi_out && !q.psi.empty())
         std::copy(q.psi.begin(), q.psi.end(), psi_out);
-    if (release && (q.state == GP_REQ_DONE || q.state == GP_REQ_FAILED)) b->reqs.erase(it);
+    if (release && (q.state == GP_REQ_DONE || q.state == GP_REQ_FAILED || q.state == GP_REQ_CANCELLED))
+        b->reqs.erase(it);
     return GP_OK;
 }
 

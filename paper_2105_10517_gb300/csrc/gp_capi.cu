@@ -11,6 +11,7 @@
 #include "../../include/gpspin.h"
 #include "gp_internal.cuh"
 
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -23,6 +24,26 @@ using namespace gpspin;
 namespace gpspin {
 
 static bool is_finite(double v) { return std::isfinite(v); }
+
+// Failure injection for the allocator: while armed with n >= 0, the n-th device
+// allocation from then on (0: the next one) fails as if the device were full,
+// once; -1 is disarmed.
+static std::atomic<long long> g_fail_after{-1};
+
+int dev_alloc(void** p, size_t bytes)
+{
+    *p = nullptr;
+    long long n = g_fail_after.load();
+    while (n >= 0 && !g_fail_after.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 0) return GP_ERR_OOM;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();  // an out-of-memory error is not sticky: clear it
+        *p = nullptr;
+        return GP_ERR_OOM;
+    }
+    return GP_OK;
+}
 
 int validate(const gp_params* p)
 {
@@ -245,15 +266,15 @@ int ensure_coef(gp_handle* h, int mode)
         if ((st = choose_tiling(p.ny, p.nx, cy, &fuy, TILE_C64_REG, 0))) return st;
     }
     if (!cs.cx) {
-        bool ok = cudaMalloc(&cs.cx, sizeof(LineCoef) * 3 * (size_t)p.ny) == cudaSuccess &&
-                  cudaMalloc(&cs.cy, sizeof(LineCoef) * 3 * (size_t)p.nx) == cudaSuccess &&
-                  cudaMalloc(&cs.ex, sizeof(double2) * p.nx) == cudaSuccess &&
-                  cudaMalloc(&cs.ey, sizeof(double2) * p.ny) == cudaSuccess;
+        bool ok = dalloc(&cs.cx, sizeof(LineCoef) * 3 * (size_t)p.ny) &&
+                  dalloc(&cs.cy, sizeof(LineCoef) * 3 * (size_t)p.nx) &&
+                  dalloc(&cs.ex, sizeof(double2) * p.nx) &&
+                  dalloc(&cs.ey, sizeof(double2) * p.ny);
         if (ok && f32)
-            ok = cudaMalloc(&cs.fx, sizeof(LineCoefF) * 3 * (size_t)p.ny) == cudaSuccess &&
-                 cudaMalloc(&cs.fy, sizeof(LineCoefF) * 3 * (size_t)p.nx) == cudaSuccess &&
-                 cudaMalloc(&cs.fex, sizeof(float2) * p.nx) == cudaSuccess &&
-                 cudaMalloc(&cs.fey, sizeof(float2) * p.ny) == cudaSuccess;
+            ok = dalloc(&cs.fx, sizeof(LineCoefF) * 3 * (size_t)p.ny) &&
+                 dalloc(&cs.fy, sizeof(LineCoefF) * 3 * (size_t)p.nx) &&
+                 dalloc(&cs.fex, sizeof(float2) * p.nx) &&
+                 dalloc(&cs.fey, sizeof(float2) * p.ny);
         if (!ok) {
             free_coef(cs);
             return GP_ERR_OOM;
@@ -499,9 +520,9 @@ int ensure_half(gp_handle* h, int mode)
     if (cs.half_valid) return GP_OK;
     const gp_params& p = h->p;
     if (!cs.cxh) {
-        bool ok = cudaMalloc(&cs.cxh, sizeof(LineCoef) * 3 * (size_t)p.ny) == cudaSuccess &&
-                  cudaMalloc(&cs.exh, sizeof(double2) * p.nx) == cudaSuccess &&
-                  cudaMalloc(&cs.eyh, sizeof(double2) * p.ny) == cudaSuccess;
+        bool ok = dalloc(&cs.cxh, sizeof(LineCoef) * 3 * (size_t)p.ny) &&
+                  dalloc(&cs.exh, sizeof(double2) * p.nx) &&
+                  dalloc(&cs.eyh, sizeof(double2) * p.ny);
         if (!ok) return GP_ERR_OOM;
     }
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
@@ -609,6 +630,7 @@ const char* gp_strerror(int s)
     case GP_ERR_UNSUPPORTED: return "parameters outside the supported range of the tabulated line solver";
     case GP_ERR_TOO_LARGE: return "grid larger than the fixed scratch of gp_propagate_noalloc (nx, ny <= 256)";
     case GP_ERR_TIMEOUT: return "a device-side wait gave up (bulk copy did not complete)";
+    case GP_ERR_QUEUE_FULL: return "the batch's queue limit is reached";
     default: return "unknown status";
     }
 }
@@ -634,17 +656,16 @@ int gp_create(const gp_params* params, void* cuda_stream, gp_handle** out)
         h->own_stream = true;
     }
     size_t n = n_elems(h);
-    bool ok = cudaMalloc(&h->psi, n * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&h->work, n * sizeof(double2)) == cudaSuccess &&
-              cudaMalloc(&h->partials, kNormBlocksMax * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&h->obs_part, (size_t)obs_blocks(h->p.nx, h->p.ny) * obs_slots() * sizeof(double)) ==
-                  cudaSuccess &&
-              cudaMalloc(&h->scal, 6 * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&h->obs_out, 8 * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&h->flag, sizeof(int)) == cudaSuccess;
+    bool ok = dalloc(&h->psi, n * sizeof(double2)) &&
+              dalloc(&h->work, n * sizeof(double2)) &&
+              dalloc(&h->partials, kNormBlocksMax * sizeof(double)) &&
+              dalloc(&h->obs_part, (size_t)obs_blocks(h->p.nx, h->p.ny) * obs_slots() * sizeof(double)) &&
+              dalloc(&h->scal, 6 * sizeof(double)) &&
+              dalloc(&h->obs_out, 8 * sizeof(double)) &&
+              dalloc(&h->flag, sizeof(int));
     if (ok && wants_fp32(h))
-        ok = cudaMalloc(&h->psi32, n * sizeof(float2)) == cudaSuccess &&
-             cudaMalloc(&h->work32, n * sizeof(float2)) == cudaSuccess;
+        ok = dalloc(&h->psi32, n * sizeof(float2)) &&
+             dalloc(&h->work32, n * sizeof(float2));
     if (!ok) {
         gp_destroy(h);
         return GP_ERR_OOM;
@@ -984,7 +1005,7 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
     const size_t bytes = n_elems(h) * (f32 ? sizeof(float2) : sizeof(double2));
     // the y-pass overwrites psi: keep a copy and restore it afterwards
     void* keep = nullptr;
-    if (cudaMalloc(&keep, bytes) != cudaSuccess) return GP_ERR_OOM;
+    if (!dalloc(&keep, bytes)) return GP_ERR_OOM;
     void* state = f32 ? (void*)h->psi32 : (void*)h->psi;
     if (cudaMemcpyAsync(keep, state, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) {
         cudaFree(keep);
@@ -1121,6 +1142,99 @@ int gp_apply_substep(gp_handle* h, int which, int mode)
         LK(launch_ypass(ay, mode, h->stream));
     }
     return sync_status(h);
+}
+
+void gp_inject_alloc_failure(long long after) { g_fail_after.store(after < 0 ? -1 : after); }
+
+// ---- checkpoints -------------------------------------------------------------
+// A checkpoint is the handle's exact device state: parameters, step count,
+// storage precision, the pending imaginary-time scale and the stored state in
+// that precision (complex128 or complex64), in host byte order.  Restoring it
+// and propagating gives bitwise the results of the uninterrupted run (same
+// library build, same tilings).
+namespace {
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    gp_params p;
+    long long steps;
+    int32_t active;
+    int32_t scale_pending;
+    double scale;
+    int32_t split;
+    int32_t mcon;
+    double m_target;
+    uint64_t state_bytes;
+};
+constexpr char kCkptMagic[8] = {'G', 'P', 'S', 'P', 'C', 'K', 'P', '1'};
+
+size_t state_bytes(const gp_handle* h)
+{
+    return n_elems(h) * (h->active == GP_FP32_MIXED ? sizeof(float2) : sizeof(double2));
+}
+}  // namespace
+
+size_t gp_checkpoint_bytes(gp_handle* h) { return h ? sizeof(CkptHeader) + state_bytes(h) : 0; }
+
+int gp_checkpoint_save(gp_handle* h, void* buf, size_t size)
+{
+    if (!h || !buf || size < gp_checkpoint_bytes(h)) return GP_ERR_ARG;
+    CkptHeader hd{};
+    std::memcpy(hd.magic, kCkptMagic, sizeof hd.magic);
+    hd.version = 1;
+    hd.header_bytes = sizeof(CkptHeader);
+    hd.p = h->p;
+    hd.steps = h->steps;
+    hd.active = h->active;
+    hd.scale_pending = h->scale_pending ? 1 : 0;
+    hd.split = h->split;
+    hd.mcon = h->mcon;
+    hd.m_target = h->m_target;
+    hd.state_bytes = state_bytes(h);
+    double scale = 1.0;
+    const void* src = h->active == GP_FP32_MIXED ? (const void*)h->psi32 : (const void*)h->psi;
+    unsigned char* out = static_cast<unsigned char*>(buf);
+    CK(cudaMemcpyAsync(&scale, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(out + sizeof(CkptHeader), src, hd.state_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    hd.scale = scale;
+    std::memcpy(out, &hd, sizeof hd);
+    return GP_OK;
+}
+
+int gp_checkpoint_load(gp_handle* h, const void* buf, size_t size)
+{
+    if (!h || !buf || size < sizeof(CkptHeader)) return GP_ERR_ARG;
+    CkptHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (std::memcmp(hd.magic, kCkptMagic, sizeof hd.magic) != 0 || hd.version != 1 ||
+        hd.header_bytes != sizeof(CkptHeader))
+        return GP_ERR_ARG;
+    const gp_params& p = hd.p;
+    if (validate(&p) != GP_OK || p.nx != h->p.nx || p.ny != h->p.ny || p.xlen != h->p.xlen ||
+        p.ylen != h->p.ylen || p.precision != h->p.precision)
+        return GP_ERR_ARG;
+    if (hd.active != GP_FP64 && hd.active != GP_FP32_MIXED) return GP_ERR_ARG;
+    if (hd.active == GP_FP32_MIXED && !h->psi32) return GP_ERR_ARG;
+    const size_t want = n_elems(h) * (hd.active == GP_FP32_MIXED ? sizeof(float2) : sizeof(double2));
+    if (hd.state_bytes != want || size < sizeof(CkptHeader) + want || !std::isfinite(hd.scale) ||
+        (hd.split != GP_SPLIT_LIE && hd.split != GP_SPLIT_STRANG))
+        return GP_ERR_ARG;
+    const unsigned char* in = static_cast<const unsigned char*>(buf) + sizeof(CkptHeader);
+    void* dst = hd.active == GP_FP32_MIXED ? (void*)h->psi32 : (void*)h->psi;
+    CK(cudaMemcpyAsync(dst, in, want, cudaMemcpyHostToDevice, h->stream));
+    LK(launch_set_scalar(h->scal, hd.scale, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->p = p;
+    h->active = hd.active;
+    h->steps = hd.steps;
+    h->scale_pending = hd.scale_pending != 0;
+    h->split = hd.split;
+    h->mcon = hd.mcon;
+    h->m_target = hd.m_target;
+    drop_graphs(h);  // the captured launches hold the previous parameters
+    return GP_OK;
 }
 
 int gp_check_wait_timeout(gp_handle* h, int polls)

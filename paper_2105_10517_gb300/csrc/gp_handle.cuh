@@ -59,6 +59,14 @@ struct gp_handle {
 namespace gpspin {
 
 // Runtime helpers (gp_capi.cu).
+// Every device allocation of the library goes through dev_alloc, which honours
+// the failure injection of gp_inject_alloc_failure.
+int dev_alloc(void** p, size_t bytes);
+template <typename T>
+bool dalloc(T** p, size_t bytes)
+{
+    return dev_alloc(reinterpret_cast<void**>(p), bytes) == GP_OK;
+}
 int ensure_coef(gp_handle* h, int mode);
 PassArgs pass_args(gp_handle* h, const CoefSet& cs, int dir);
 PassArgsF pass_args_f32(gp_handle* h, const CoefSet& cs, int dir);

@@ -29,14 +29,16 @@ FP64, FP32_MIXED = 0, 1
 SUB_P, SUB_X, SUB_Y = 0, 1, 2
 
 STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP_ERR_NONFINITE",
-          5: "GP_ERR_UNSUPPORTED", 6: "GP_ERR_TOO_LARGE", 7: "GP_ERR_TIMEOUT"}
+          5: "GP_ERR_UNSUPPORTED", 6: "GP_ERR_TOO_LARGE", 7: "GP_ERR_TIMEOUT", 8: "GP_ERR_QUEUE_FULL"}
 
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
            "gp_init_winding", "gp_set_magnetization", "gp_set_splitting", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
            "gp_tiling_info", "gp_set_tiling", "gp_plan_tiling", "gp_check_wait_timeout",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
-           "gp_batch_step", "gp_batch_poll", "gp_strerror"]
+           "gp_batch_step", "gp_batch_poll", "gp_batch_set_queue_limit", "gp_batch_cancel", "gp_batch_error",
+           "gp_inject_alloc_failure", "gp_checkpoint_bytes", "gp_checkpoint_save", "gp_checkpoint_load",
+           "gp_strerror"]
 
 
 def _nvcc():
@@ -120,7 +122,7 @@ class Request(ctypes.Structure):
 
 
 POLICY_FP64, POLICY_FP32_REFINE = 0, 1
-REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_UNKNOWN = 0, 1, 2, 3, 4
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_UNKNOWN, REQ_CANCELLED = 0, 1, 2, 3, 4, 5
 
 _lib = None
 
@@ -175,8 +177,20 @@ def load():
     lib.gp_batch_step.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.gp_batch_poll.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(Obs), dp, ip]
-    for name in ("gp_batch_create", "gp_batch_submit", "gp_batch_step", "gp_batch_poll"):
+    lib.gp_batch_set_queue_limit.argtypes = [vp, ip]
+    lib.gp_batch_cancel.argtypes = [vp, ctypes.c_longlong]
+    lib.gp_batch_error.argtypes = [vp, ctypes.c_longlong]
+    for name in ("gp_batch_create", "gp_batch_submit", "gp_batch_step", "gp_batch_poll", "gp_batch_set_queue_limit",
+                 "gp_batch_cancel", "gp_batch_error"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.gp_inject_alloc_failure.argtypes = [ctypes.c_longlong]
+    lib.gp_inject_alloc_failure.restype = None
+    lib.gp_checkpoint_bytes.argtypes = [vp]
+    lib.gp_checkpoint_bytes.restype = ctypes.c_size_t
+    lib.gp_checkpoint_save.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.gp_checkpoint_save.restype = ctypes.c_int
+    lib.gp_checkpoint_load.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.gp_checkpoint_load.restype = ctypes.c_int
     lib.gp_strerror.argtypes = [ip]
     lib.gp_strerror.restype = ctypes.c_char_p
     for name in ("gp_create", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
@@ -220,6 +234,12 @@ def propagate_noalloc(params, psi_dev_ptr, nsteps, mode=IMAG, stream=None):
     s = ctypes.c_void_p(int(stream)) if stream is not None else None
     _check(load().gp_propagate_noalloc(ctypes.byref(p), ctypes.c_void_p(int(psi_dev_ptr)), int(nsteps), int(mode), s),
            "gp_propagate_noalloc")
+
+
+def inject_alloc_failure(after):
+    """Make the after-th device allocation of the library from now on fail once
+    (0: the next one); after < 0 disarms (tests of out-of-memory handling)."""
+    load().gp_inject_alloc_failure(int(after))
 
 
 def plan_tiling(params, mode=IMAG):
@@ -369,6 +389,27 @@ class Solver:
                              ctas=v[6], register_solve=bool(v[7]))
         return out
 
+    def checkpoint(self):
+        """The handle's exact state as bytes (gp_checkpoint_save)."""
+        n = int(load().gp_checkpoint_bytes(self._h))
+        buf = ctypes.create_string_buffer(n)
+        _check(load().gp_checkpoint_save(self._h, ctypes.cast(buf, ctypes.c_void_p), n), "gp_checkpoint_save")
+        return buf.raw
+
+    def restore(self, data):
+        """Restore a checkpoint made by checkpoint() (same grid and precision)."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        _check(load().gp_checkpoint_load(self._h, ctypes.cast(buf, ctypes.c_void_p), len(data)),
+               "gp_checkpoint_load")
+
+    def save_checkpoint(self, path):
+        with open(path, "wb") as f:
+            f.write(self.checkpoint())
+
+    def load_checkpoint(self, path):
+        with open(path, "rb") as f:
+            self.restore(f.read())
+
     def check_wait_timeout(self, polls=64):
         """Run the passes' bounded device wait on a barrier nothing completes
         (raises GPError with GP_ERR_TIMEOUT, as a propagate whose copy wait gave up)."""
@@ -424,6 +465,18 @@ class Batch:
                "gp_batch_submit")
         self._shape[rid.value] = (3, int(params["ny"]), int(params["nx"]))
         return rid.value
+
+    def set_queue_limit(self, max_queued):
+        """Refuse submissions (GP_ERR_QUEUE_FULL) while max_queued requests wait; 0: no limit."""
+        _check(load().gp_batch_set_queue_limit(self._b, int(max_queued)), "gp_batch_set_queue_limit")
+
+    def cancel(self, rid):
+        """Cancel a queued or running solve (its device memory is released at once)."""
+        _check(load().gp_batch_cancel(self._b, int(rid)), "gp_batch_cancel")
+
+    def error(self, rid):
+        """The status that failed a REQ_FAILED solve (0 otherwise)."""
+        return int(load().gp_batch_error(self._b, int(rid)))
 
     def step(self):
         nr, nq = ctypes.c_int(), ctypes.c_int()

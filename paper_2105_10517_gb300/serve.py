@@ -16,17 +16,29 @@ import numpy as np
 from . import gpspin
 
 
+def _pct(v, q):
+    return float(np.percentile(np.array(v), q)) if len(v) else None
+
+
 def _summary(records, makespan):
-    lat = np.array([r["latency"] for r in records])
-    capped = sum(1 for r in records if r["steps"] >= r["cap"])
-    return dict(solves=len(records), makespan_s=makespan, solves_per_s=len(records) / makespan,
-                p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
-                capped=capped, failed=sum(1 for r in records if r["state"] != gpspin.REQ_DONE))
+    done = [r for r in records if r["state"] == gpspin.REQ_DONE]
+    conv = [r["latency"] for r in done if r["steps"] < r["cap"]]
+    cap = [r["latency"] for r in done if r["steps"] >= r["cap"]]
+    lat = [r["latency"] for r in done]
+    return dict(solves=len(done), makespan_s=makespan, solves_per_s=len(done) / makespan,
+                p50_s=_pct(lat, 50), p99_s=_pct(lat, 99),
+                converged=len(conv), p50_converged_s=_pct(conv, 50), p99_converged_s=_pct(conv, 99),
+                capped=len(cap), p50_capped_s=_pct(cap, 50), p99_capped_s=_pct(cap, 99),
+                failed=sum(1 for r in records if r["state"] == gpspin.REQ_FAILED),
+                cancelled=sum(1 for r in records if r["state"] == gpspin.REQ_CANCELLED))
 
 
 def serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=64 << 30, check_every=100, tol=1e-9,
-                  tol32=1e-7, cap=20000, refine_steps=2000, stream=None):
-    """Continuous batching over the trace; returns (summary, per-request records)."""
+                  tol32=1e-7, cap=20000, refine_steps=2000, stream=None, deadline_s=None):
+    """Continuous batching over the trace; returns (summary, per-request records).
+    With deadline_s, a request still queued or running that long after its
+    arrival is cancelled (its memory is released for the others) and recorded
+    as REQ_CANCELLED."""
     pending = sorted(trace, key=lambda r: r["arrival"])
     records, live = [], {}
     with gpspin.Batch(max_bytes, check_every=check_every, stream=stream) as b:
@@ -47,7 +59,11 @@ def serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=64 << 30, c
             done_t = time.perf_counter() - t0
             for rid in list(live):
                 st, steps, obs, _ = b.poll(rid)
-                if st in (gpspin.REQ_DONE, gpspin.REQ_FAILED):
+                if (deadline_s is not None and st in (gpspin.REQ_QUEUED, gpspin.REQ_RUNNING)
+                        and done_t - live[rid]["arrival"] > deadline_s):
+                    b.cancel(rid)
+                    st = gpspin.REQ_CANCELLED
+                if st in (gpspin.REQ_DONE, gpspin.REQ_FAILED, gpspin.REQ_CANCELLED):
                     rq = live.pop(rid)
                     b.poll(rid, release=True)
                     records.append(dict(arrival=rq["arrival"], done=done_t, latency=done_t - rq["arrival"],
