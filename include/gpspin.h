@@ -253,6 +253,10 @@ void gp_batch_destroy(gp_batch* b);
 /* Queues a solve (params.precision is set from the policy); *id_out identifies it.
  * GP_ERR_QUEUE_FULL if the queue limit (gp_batch_set_queue_limit) is reached. */
 int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req, long long* id_out);
+/* Ticks are captured as CUDA graphs and replayed while the set of running
+ * solves is unchanged (the default, enable != 0); enable = 0 launches every
+ * kernel of every tick directly.  Results are bitwise the same either way. */
+int gp_batch_use_graphs(gp_batch* b, int enable);
 /* Limits the number of queued (not yet admitted) requests; 0: no limit. */
 int gp_batch_set_queue_limit(gp_batch* b, int max_queued);
 /* Cancels a queued or running solve between ticks: a queued one leaves the

@@ -99,6 +99,38 @@ struct Group {
     std::vector<FinArgs> fin;
     DevBuf<PassArgsT<C>> dax, day;
     DevBuf<FinArgs> dfin;
+    // CUDA graph of one tick's launches and the launch lists it was captured for:
+    // replayed while the running set (and so every argument) is unchanged
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> sig;
+    void drop_graph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        sig.clear();
+    }
+    // bytes of everything the tick's launches read: pass and finalize arguments,
+    // work lists, steps per tick
+    std::vector<unsigned char> signature(int steps) const
+    {
+        std::vector<unsigned char> v;
+        auto put = [&v](const void* p, size_t n) {
+            const unsigned char* c = static_cast<const unsigned char*>(p);
+            v.insert(v.end(), c, c + n);
+        };
+        put(&steps, sizeof steps);
+        put(ax.data(), ax.size() * sizeof(ax[0]));
+        put(ay.data(), ay.size() * sizeof(ay[0]));
+        put(fin.data(), fin.size() * sizeof(fin[0]));
+        for (int c = 0; c < kSolveClasses; ++c) {
+            const size_t nx = lx[c].items.size(), ny = ly[c].items.size();
+            put(&nx, sizeof nx);
+            put(lx[c].items.data(), nx * sizeof(int2));
+            put(&ny, sizeof ny);
+            put(ly[c].items.data(), ny * sizeof(int2));
+        }
+        return v;
+    }
     void clear()
     {
         ax.clear();
@@ -111,6 +143,7 @@ struct Group {
     }
     void release()
     {
+        drop_graph();
         dax.release();
         day.release();
         for (int c = 0; c < kSolveClasses; ++c) {
@@ -136,6 +169,9 @@ struct gp_batch {
     int* counts = nullptr;  // device: kGroupCounts per precision group (complex128, complex64)
     int* flag = nullptr;
     int max_queued = 0;     // 0: no limit on queued requests
+    bool graphs = true;     // replay captured ticks while the running set is unchanged
+    cudaStream_t stream32 = nullptr;  // the complex64 group runs beside the complex128 one
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -166,14 +202,53 @@ void add_instance(Group<C>& g, gp_handle* h, const PassArgsT<C>& ax, PassArgsT<C
     g.fin.push_back(FinArgs{h->partials, y_blocks(ay.t), cell(h), h->scal});
 }
 
+// The launches of `steps` steps of one group: per step the x-passes of every
+// solve kind, the y-passes, then the normalisation of every instance.
 template <typename C>
-int upload_and_run(gp_batch* b, Group<C>& g, int* counts, int steps)
+int enqueue_group(gp_batch* b, Group<C>& g, int* counts, int steps, cudaStream_t s)
 {
-    if (g.ax.empty()) return GP_OK;
+    const int n_inst = (int)g.fin.size();
+    for (int k = 0; k < steps; ++k) {
+        for (int c = 0; c < kSolveClasses; ++c) {
+            const PassList& l = g.lx[c];
+            if (!l.items.empty() && launch_xpass_batched(g.dax.p, l.d.p, counts + c, (int)l.items.size(), l.threads,
+                                                         l.smem, GP_IMAG, s, kClassM[c]))
+                return GP_ERR_CUDA;
+        }
+        for (int c = 0; c < kSolveClasses; ++c) {
+            const PassList& l = g.ly[c];
+            if (!l.items.empty() && launch_ypass_batched(g.day.p, l.d.p, counts + kSolveClasses + c,
+                                                         (int)l.items.size(), l.threads, l.smem, GP_IMAG, s,
+                                                         kClassM[c]))
+                return GP_ERR_CUDA;
+        }
+        if (launch_finalize_norm_batched(g.dfin.p, counts + 2 * kSolveClasses, n_inst, b->flag, s)) return GP_ERR_CUDA;
+    }
+    return GP_OK;
+}
+
+// One tick of a group on stream s.  While the running set is unchanged the tick
+// replays the CUDA graph captured for it; after a change the launch lists are
+// uploaded, the tick runs directly and is captured for the next ticks.
+template <typename C>
+int upload_and_run(gp_batch* b, Group<C>& g, int* counts, int steps, cudaStream_t s)
+{
+    if (g.ax.empty()) {
+        g.drop_graph();
+        return GP_OK;
+    }
+    std::vector<unsigned char> sig;
+    if (b->graphs) {
+        sig = g.signature(steps);
+        if (g.exec && sig == g.sig) {
+            BK(cudaGraphLaunch(g.exec, s));
+            return GP_OK;
+        }
+    }
+    g.drop_graph();
     int st;
     if ((st = g.dax.reserve(g.ax.size())) || (st = g.day.reserve(g.ay.size())) || (st = g.dfin.reserve(g.fin.size())))
         return st;
-    cudaStream_t s = b->stream;
     int n[kGroupCounts];
     for (int c = 0; c < kSolveClasses; ++c) {
         PassList* lists[2] = {&g.lx[c], &g.ly[c]};
@@ -190,22 +265,21 @@ int upload_and_run(gp_batch* b, Group<C>& g, int* counts, int steps)
     BK(cudaMemcpyAsync(g.day.p, g.ay.data(), g.ay.size() * sizeof(g.ay[0]), cudaMemcpyHostToDevice, s));
     BK(cudaMemcpyAsync(g.dfin.p, g.fin.data(), g.fin.size() * sizeof(FinArgs), cudaMemcpyHostToDevice, s));
     BK(cudaMemcpyAsync(counts, n, sizeof(n), cudaMemcpyHostToDevice, s));
-    for (int k = 0; k < steps; ++k) {
-        for (int c = 0; c < kSolveClasses; ++c) {
-            const PassList& l = g.lx[c];
-            if (!l.items.empty() && launch_xpass_batched(g.dax.p, l.d.p, counts + c, (int)l.items.size(), l.threads,
-                                                         l.smem, GP_IMAG, s, kClassM[c]))
-                return GP_ERR_CUDA;
+    // the direct launches also set the kernels' shared-memory attributes, which
+    // the captured launches then find in place
+    if ((st = enqueue_group(b, g, counts, steps, s))) return st;
+    if (b->graphs) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int cst = enqueue_group(b, g, counts, steps, s);
+            const cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (cst == GP_OK && e == cudaSuccess && graph && cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess)
+                g.sig.swap(sig);
+            else
+                g.exec = nullptr;
+            if (graph) cudaGraphDestroy(graph);
         }
-        for (int c = 0; c < kSolveClasses; ++c) {
-            const PassList& l = g.ly[c];
-            if (!l.items.empty() && launch_ypass_batched(g.day.p, l.d.p, counts + kSolveClasses + c,
-                                                         (int)l.items.size(), l.threads, l.smem, GP_IMAG, s,
-                                                         kClassM[c]))
-                return GP_ERR_CUDA;
-        }
-        if (launch_finalize_norm_batched(g.dfin.p, counts + 2 * kSolveClasses, n[2 * kSolveClasses], b->flag, s))
-            return GP_ERR_CUDA;
+        cudaGetLastError();  // a failed capture only means direct launches next tick
     }
     return GP_OK;
 }
@@ -304,6 +378,12 @@ int gp_batch_create(size_t max_device_bytes, int check_every, void* cuda_stream,
         gp_batch_destroy(b);
         return GP_ERR_OOM;
     }
+    if (cudaStreamCreateWithFlags(&b->stream32, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        gp_batch_destroy(b);
+        return GP_ERR_CUDA;
+    }
     *out = b;
     return GP_OK;
 }
@@ -314,10 +394,14 @@ void gp_batch_destroy(gp_batch* b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     for (auto& kv : b->reqs)
         if (kv.second.h) gp_destroy(kv.second.h);
+    if (b->stream32) cudaStreamSynchronize(b->stream32);
     b->g64.release();
     b->g32.release();
     cudaFree(b->counts);
     cudaFree(b->flag);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->stream32) cudaStreamDestroy(b->stream32);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -371,8 +455,14 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
     }
     const int k = b->check_every;
     if (!run.empty()) {
-        if ((st = upload_and_run(b, b->g64, b->counts, k))) return st;
-        if ((st = upload_and_run(b, b->g32, b->counts + kGroupCounts, k))) return st;
+        // the complex64 group runs on its own stream, after everything the
+        // handles enqueued on the batch stream, and the batch stream waits for it
+        BK(cudaEventRecord(b->ev_fork, b->stream));
+        BK(cudaStreamWaitEvent(b->stream32, b->ev_fork, 0));
+        if ((st = upload_and_run(b, b->g64, b->counts, k, b->stream))) return st;
+        if ((st = upload_and_run(b, b->g32, b->counts + kGroupCounts, k, b->stream32))) return st;
+        BK(cudaEventRecord(b->ev_join, b->stream32));
+        BK(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
         BK(cudaStreamSynchronize(b->stream));
     }
     // convergence checks between ticks
@@ -414,6 +504,17 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
         if (n_queued) *n_queued = (int)b->queue.size();
     }
     return st;
+}
+
+int gp_batch_use_graphs(gp_batch* b, int enable)
+{
+    if (!b) return GP_ERR_ARG;
+    b->graphs = enable != 0;
+    if (!b->graphs) {
+        b->g64.drop_graph();
+        b->g32.drop_graph();
+    }
+    return GP_OK;
 }
 
 int gp_batch_set_queue_limit(gp_batch* b, int max_queued)

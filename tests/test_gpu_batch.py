@@ -25,10 +25,11 @@ def req_params(n, **kw):
     return p
 
 
-def run_batch(items, max_bytes=8 << 30):
+def run_batch(items, max_bytes=8 << 30, graphs=True):
     """items: list of (params, submit kwargs); runs until all are done."""
     out = {}
     with gpspin.Batch(max_bytes, check_every=CHECK) as b:
+        b.use_graphs(graphs)
         ids = [b.submit(p, **kw) for p, kw in items]
         for _ in range(10000):
             nr, nq = b.step()
@@ -103,3 +104,20 @@ def test_mixed_precision_policy_agrees_with_fp64():
     assert r64[0] == r32[0] == gpspin.REQ_DONE
     e64, e32 = r64[2]["energy"], r32[2]["energy"]
     assert abs(e32 - e64) <= 1e-6 * abs(e64)
+
+
+def test_graph_ticks_equal_direct_ticks_bitwise():
+    """Ticks replayed from captured CUDA graphs give bitwise the results of ticks
+    whose kernels are launched directly, with both precision groups running (on
+    their two streams) and the running set changing as solves finish."""
+    items = [
+        (req_params(64, c2=12.0, so_type=2), dict(seed=3, tol=1e-300, cap=60)),
+        (req_params(96), dict(seed=11, tol=1e-300, cap=140)),
+        (req_params(128, omeg=0.8), dict(seed=5, tol=1e-300, cap=100, policy=gpspin.POLICY_FP32_REFINE,
+                                         refine_steps=40)),
+    ]
+    a = run_batch(items, graphs=True)
+    b = run_batch(items, graphs=False)
+    for x, y in zip(a, b):
+        assert x[0] == y[0] == gpspin.REQ_DONE and x[1] == y[1]
+        assert np.array_equal(x[3], y[3])
