@@ -228,8 +228,6 @@ def kernel_name(dom, mode, prec, tiles, strang):
     td = tiles[dom]
     if strang and dom == "xpass":
         return f"xpass_kernel<{mode}, double2> + xtail_kernel<{mode}> (both x-passes of a second-order step)"
-    if td.get("pipelined"):
-        return f"{dom}_pipe<{mode}, {td['chunk']}>"
     if td.get("register_solve"):
         return f"{dom}_kernel_reg<{mode}, float2, {td['chunk']}>"
     return f"{dom}_kernel<{mode}, {'float2' if prec == 'fp32' else 'double2'}>"

@@ -288,23 +288,17 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out);
 /* Sets the tiling of one pass (dir 0: x-pass, 1: y-pass) for the handle's current
  * precision and the given mode: cluster = CTAs per line group (1, 2, 4 or 8),
  * lines_per_cta, chunk = minimum chunk length of the parallel Thomas solve
- * (raised to what the precision needs), pipelined != 0 = a complex64 pass with
- * the register-resident solve runs persistently, staging the next line group
- * while it computes the current one (when the line count is a multiple of
- * lines_per_cta; bitwise the same results as one group per CTA; ignored for
- * complex128).  GP_ERR_ARG or GP_ERR_UNSUPPORTED if the tiling does not fit
- * (threads, shared memory, chunks per CTA).  Results stay within the parity
- * tolerances for every valid tiling. */
-int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk, int pipelined);
+ * (raised to what the precision needs).  GP_ERR_ARG or GP_ERR_UNSUPPORTED if
+ * the tiling does not fit (threads, shared memory, chunks per CTA).  Results
+ * stay within the parity tolerances for every valid tiling. */
+int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk);
 
 /* The tiling the handle uses for a pass (dir 0: x-pass, 1: y-pass) in the given
  * mode and its current precision: out[0] CTAs per line group (cluster size),
  * out[1] lines per CTA, out[2] chunk length, out[3] chunks per line, out[4]
  * threads per CTA, out[5] dynamic shared memory bytes, out[6] CTAs per launch,
  * out[7] solve kind: 0 shared-memory line arrays, 1 register-resident chunks
- * (complex64, chunk length 16, 24 or 32), 2 register-resident chunks in a
- * persistent pass that stages the next line group while it computes the
- * current one.  out must hold 8 ints. */
+ * (complex64, chunk length 16, 24 or 32).  out must hold 8 ints. */
 int gp_tiling_info(gp_handle* h, int mode, int dir, int* out);
 
 /* The default tiling of a pass (dir 0: x-pass, 1: y-pass) for these parameters

@@ -120,9 +120,7 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
 {
     if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
     if (S < 1 || S > 8 || (S & (S - 1)) || R < 1) return GP_ERR_ARG;  // portable cluster sizes
-    if (kind < TILE_C128 || kind > TILE_C64_PIPE) return GP_ERR_ARG;
-    const bool pipe = kind == TILE_C64_PIPE;
-    if (pipe) kind = TILE_C64_REG;
+    if (kind < TILE_C128 || kind > TILE_C64_REG) return GP_ERR_ARG;
     const bool c64 = kind != TILE_C128;
     const double bits = c64 ? 26.0 : 60.0;
     const size_t elem = c64 ? sizeof(float2) : sizeof(double2);
@@ -133,7 +131,6 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
     m = (m + 3) / 4 * 4;
     if (kind == TILE_C64_REG && m <= 32) m = m <= 16 ? 16 : (m <= 24 ? 24 : 32);
     const bool single = kind == TILE_C64_REG && m <= 32;
-    const bool persist = pipe && single && nlines % R == 0;
     int Q = (L + m - 1) / m;
     if (S > 1 && Q < 2 * S) return GP_ERR_ARG;  // at least two chunks per CTA
     const int Qc = (Q + S - 1) / S;
@@ -159,7 +156,7 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
     const size_t line_bytes = up(3 * R * Lp * elem);
     // carries: cf, cb (3R Qc each) and, after cb, the two 3R-slot halos that
     // the cluster neighbours push into (register-resident solve)
-    const size_t smem = line_bytes * (single && !persist ? 1 : 2) + 2 * up(3 * R * Qc * elem) + up(2 * 3 * R * elem);
+    const size_t smem = line_bytes * (single ? 1 : 2) + 2 * up(3 * R * Qc * elem) + up(2 * 3 * R * elem);
     if (smem > 227 * 1024) return GP_ERR_UNSUPPORTED;
     t->L = L;
     t->nlines = nlines;
@@ -173,12 +170,11 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
     t->Lp = Lp;
     t->threads = std::min(512, (std::max(32, 3 * R * Qc) + 31) / 32 * 32);
     t->smem = smem;
-    t->off_b = single && !persist ? 0 : line_bytes;
-    t->off_cf = line_bytes * (single && !persist ? 1 : 2);
+    t->off_b = single ? 0 : line_bytes;
+    t->off_cf = line_bytes * (single ? 1 : 2);
     t->off_cb = t->off_cf + up(3 * R * Qc * elem);
     t->bulk = 0;  // set per pass by the caller (needs 16-byte aligned rows)
     t->single = single ? 1 : 0;
-    t->persist = persist ? 1 : 0;
     return GP_OK;
 }
 
@@ -264,8 +260,8 @@ int ensure_coef(gp_handle* h, int mode)
     if ((st = choose_tiling(p.nx, p.ny, cx, &ux, TILE_C128, 0))) return st;
     if ((st = choose_tiling(p.ny, p.nx, cy, &uy, TILE_C128, 0))) return st;
     if (f32) {
-        if ((st = choose_tiling(p.nx, p.ny, cx, &ftx, TILE_C64_PIPE))) return st;
-        if ((st = choose_tiling(p.ny, p.nx, cy, &fty, TILE_C64_PIPE))) return st;
+        if ((st = choose_tiling(p.nx, p.ny, cx, &ftx, TILE_C64_REG))) return st;
+        if ((st = choose_tiling(p.ny, p.nx, cy, &fty, TILE_C64_REG))) return st;
         if ((st = choose_tiling(p.nx, p.ny, cx, &fux, TILE_C64_REG, 0))) return st;  // batched launches
         if ((st = choose_tiling(p.ny, p.nx, cy, &fuy, TILE_C64_REG, 0))) return st;
     }
@@ -1023,14 +1019,13 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
         LineTiling best = cur;
         float best_ms = -1.0f;
         const int ms_add[] = {0, 4, 8, 16, 32};
-        for (int kind : {TILE_C128, TILE_C64_REG, TILE_C64_PIPE})
         for (int S : {1, 2, 4, 8})
             for (int R : {1, 2, 4, 8})
                 for (int add : ms_add) {
-                    if ((kind == TILE_C128) == f32) continue;
                     LineTiling t;
-                    if (make_tiling(L, nl, cp, kind, S, R, cur.m - (cur.m % 4) + add, &t) != GP_OK) continue;
-                    if (kind == TILE_C64_PIPE && !t.persist) continue;
+                    if (make_tiling(L, nl, cp, f32 ? TILE_C64_REG : TILE_C128, S, R, cur.m - (cur.m % 4) + add, &t) !=
+                        GP_OK)
+                        continue;
                     if (S > 1 && L < 64) continue;
                     float ms;
                     if (f32) {
@@ -1069,7 +1064,7 @@ int gp_plan_tiling(const gp_params* p, int mode, int dir, int* out)
     int st = validate(p);
     if (st) return st;
     const int L = dir == 0 ? p->nx : p->ny, nl = dir == 0 ? p->ny : p->nx;
-    const int kind = p->precision == GP_FP32_MIXED ? TILE_C64_PIPE : TILE_C128;
+    const int kind = p->precision == GP_FP32_MIXED ? TILE_C64_REG : TILE_C128;
     LineTiling t;
     if ((st = choose_tiling(L, nl, max_cp(*p, dir, mode), &t, kind))) return st;
     const int unit = t.single ? 2 : 1, G = t.single ? 8 : (kind == TILE_C128 ? 8 : 16);
@@ -1080,7 +1075,7 @@ int gp_plan_tiling(const gp_params* p, int mode, int dir, int* out)
     out[4] = t.threads;
     out[5] = (int)t.smem;
     out[6] = y_blocks(t);
-    out[7] = t.single + t.persist;
+    out[7] = t.single;
     out[8] = t.F;
     out[9] = t.cs;
     out[10] = t.Lp;
@@ -1088,7 +1083,7 @@ int gp_plan_tiling(const gp_params* p, int mode, int dir, int* out)
     return GP_OK;
 }
 
-int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk, int pipelined)
+int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk)
 {
     if (!h || (mode != GP_IMAG && mode != GP_REAL) || dir < 0 || dir > 1) return GP_ERR_ARG;
     int st = ensure_coef(h, mode);
@@ -1098,7 +1093,7 @@ int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_ct
     const bool f32 = h->active == GP_FP32_MIXED;
     LineTiling t;
     st = make_tiling(dir == 0 ? p.nx : p.ny, dir == 0 ? p.ny : p.nx, max_cp(p, dir, mode),
-                     f32 ? (pipelined ? TILE_C64_PIPE : TILE_C64_REG) : TILE_C128, cluster, lines_per_cta, chunk, &t);
+                     f32 ? TILE_C64_REG : TILE_C128, cluster, lines_per_cta, chunk, &t);
     if (st) return st;
     (f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty)) = t;
     drop_graphs(h);
@@ -1120,7 +1115,7 @@ int gp_tiling_info(gp_handle* h, int mode, int dir, int* out)
     out[4] = t.threads;
     out[5] = (int)t.smem;
     out[6] = y_blocks(t);
-    out[7] = t.single + t.persist;
+    out[7] = t.single;
     return GP_OK;
 }
 

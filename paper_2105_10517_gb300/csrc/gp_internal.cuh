@@ -73,16 +73,11 @@ struct LineTiling {
     size_t off_cb;
     int bulk;      // rows are 16-byte aligned: stage them with cp.async.bulk
     int single;    // one line array: rows are staged in place (complex64 register-resident solve, m = 16/24/32)
-    int persist;   // persistent pipelined pass (complex64, single, nlines % R == 0): each cluster walks over
-                   // line groups and stages the next group into a second line array (at off_b) while it
-                   // computes the current one
 };
 
 // Kinds of tiling: complex128; complex64 with the shared-memory solve (two line
 // arrays, any chunk length); complex64 with the register-resident solve.
-// TILE_C64_PIPE: the register-resident solve in a persistent pass that stages the
-// next line group while it computes the current one (when the groups are full).
-enum TileKind { TILE_C128 = 0, TILE_C64 = 1, TILE_C64_REG = 2, TILE_C64_PIPE = 3 };
+enum TileKind { TILE_C128 = 0, TILE_C64 = 1, TILE_C64_REG = 2 };
 
 template <typename C>
 struct PassArgsT {

@@ -10,11 +10,8 @@
 // Taylor polynomials, and the tridiagonal solves are split into chunks that
 // many threads run at once (the chunked Thomas solve below).
 #include "gp_internal.cuh"
-#include <algorithm>
 #include <cmath>
 #include <cooperative_groups.h>
-#include <mutex>
-#include <vector>
 
 namespace cg = cooperative_groups;
 
@@ -99,13 +96,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity)
 // still writing its shared memory, and returns false.
 constexpr int kWaitTries = 1 << 22;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err, int tries = kWaitTries, uint32_t parity = 0)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err, int tries = kWaitTries)
 {
     bool ok = false;
-    for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, parity);
+    for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, 0);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && err) atomicOr(err, 8);
-        for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, parity);
+        for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, 0);
         __syncthreads();
         return false;
     }
@@ -160,15 +157,15 @@ __device__ __forceinline__ void push_carry(float2 v, float2* slot, uint64_t* bar
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(b) : "memory");
 }
 
-__device__ __forceinline__ void wait_carry(uint64_t* bar, int* err, uint32_t parity = 0)
+__device__ __forceinline__ void wait_carry(uint64_t* bar, int* err)
 {
     uint32_t ok = 0;
     for (int it = 0; it < kWaitTries && !ok; ++it)
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
+            : "r"(smem_u32(bar))
             : "memory");
     if (!ok && err) atomicOr(err, 8);
 }
@@ -699,15 +696,10 @@ __device__ __forceinline__ ConvCoef<C> load_conv(const LineCoefT<C>* coef, const
 // Chunks q >= 1 start at row m >= H + F, past the rows where the factorisation
 // still differs from its limit (H rows) and where the fixup powers matter, so
 // they use the converged coefficients throughout; chunk 0 takes the table rows.
-// In a persistent pass the cluster runs this once per line group: `first` holds
-// the wait half of the start barrier (first group only), `last` the arrive half of
-// the exit barrier (last group only), and the carry mbarriers complete one phase
-// per group (parity cpar).
 template <int MODE, typename C, int M>
 __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const LineCoefT<C>* coef,
                                                    const ConvCoef<C>& cc, const LineTiling& T, const Part& P,
-                                                   C* hf, C* hb, uint64_t* cbar, int* err, bool first = true,
-                                                   bool last = true, uint32_t cpar = 0)
+                                                   C* hf, C* hb, uint64_t* cbar, int* err)
 {
     typedef typename RealOf<C>::type R;
     static_assert(sizeof(C) == 8 && M % 2 == 0, "pairs of complex64 per 16-byte shared-memory access");
@@ -764,7 +756,7 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
         cf[lc * Qc + ql] = y[M - 1];
     }
     if (T.S > 1) {
-        if (first) cluster_wait();  // start barrier: the neighbours' mbarriers are initialised
+        cluster_wait();  // start barrier: the neighbours' mbarriers are initialised
         if (active && ql == P.nq - 1 && P.rank < T.S - 1) push_carry(y[M - 1], hf + lc, cbar, P.rank + 1);
     }
     __syncthreads();
@@ -774,7 +766,7 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
             if (ql > 0) {
                 yc = cf[lc * Qc + ql - 1];
             } else {  // q > 0 with ql == 0: a cluster rank > 0
-                wait_carry(cbar, err, cpar);
+                wait_carry(cbar, err);
                 yc = hf[lc];
             }
             const int nf = min(F, len);
@@ -815,7 +807,7 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
     // No CTA of the cluster may leave while a neighbour's store into its shared
     // memory can be in flight: this CTA's stores are done here (arrive), and the
     // matching cluster_wait() closes the pass, overlapping the store phase.
-    if (T.S > 1 && last) cluster_arrive();
+    if (T.S > 1) cluster_arrive();
     __syncthreads();
     if (active) {
         if (q < Q - 1) {  // full chunk (len == M): the last F points take the backward fixup
@@ -823,7 +815,7 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
             if (ql < P.nq - 1) {
                 wc = cb[lc * Qc + ql + 1];
             } else {  // the last chunk of a CTA that is not the line's last: rank < S - 1
-                wait_carry(cbar + 1, err, cpar);
+                wait_carry(cbar + 1, err);
                 wc = hb[lc];
             }
             if constexpr (sizeof(R) == 4) {
@@ -1090,10 +1082,6 @@ __global__ void __launch_bounds__(512) xtail_kernel(PassArgs A)
 // With the register-resident solve of chunk length M (one-array tilings).  The
 // register caps (a few dozen bytes of spill at most) keep five to ten CTAs per SM.
 constexpr int reg_cap(int M) { return M == 16 ? 64 : (M == 24 ? 80 : 96); }
-// The persistent passes keep the group walk's state live across the loop: a
-// higher cap (their double-buffered shared memory already limits them to a few
-// CTAs per SM, so the registers do not lower the occupancy further).
-constexpr int reg_cap_pipe(int M) { return M == 16 ? 96 : (M == 24 ? 112 : 128); }
 
 template <int MODE, typename C, int M>
 __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) xpass_kernel_reg(PassArgsT<C> A)
@@ -1295,282 +1283,6 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
     ypass_body<MODE, C, M>(A, it.y, smem_raw, mbar, wsum, cbar);
 }
 
-// ---------------------------------------------- persistent complex64 passes --
-// The complex64 passes are bound by HBM bandwidth.  A CTA (or cluster) that
-// stages, computes and stores a single line group alternates between memory and
-// arithmetic, and the CTAs of a wave do so in step, so the two add up instead of
-// overlapping.  These passes keep one cluster of S CTAs (or one CTA) per
-// resident slot and walk it over the line groups g = cluster, cluster + clusters,
-// ...: the bulk-copy engine stages the chunks of the next group into the second
-// line array while the current group is computed, and the global stores of a
-// group drain while the next one is computed.  Per group, the arithmetic, the
-// thread mapping and the partial-norm order are those of the one-group passes,
-// so both give bitwise the same results.  Every group is full (nlines % R == 0),
-// which keeps the carry mbarriers' arrival counts the same for every group.
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Bulk copies of one group's chunks (one per chunk, issued by the thread that
-// solves it) into dst; thread 0 announces the bytes on mbar.  No barrier is
-// needed between the announcement and the copies: a copy that completes first
-// leaves the transaction count transiently negative, and the phase cannot
-// complete before thread 0 has arrived.
-template <typename C>
-__device__ __forceinline__ void issue_chunks(C* dst, const C* base, size_t plane, const LineTiling& T, const Part& P,
-                                             uint64_t* mbar)
-{
-    if (threadIdx.x == 0) mbar_expect_tx(mbar, (uint32_t)(3 * P.nl * P.len * sizeof(C)));
-    const int nl3 = 3 * P.nl, nq = (P.len + T.m - 1) / T.m;
-    for (int u = threadIdx.x; u < nl3 * nq; u += blockDim.x) {
-        const int ql = u / nl3, lc = u - ql * nl3, r = lc / 3, c = lc - 3 * r;
-        const int k = ql * T.m, n = min(T.m, P.len - k);
-        bulk_g2s(dst + lc * T.Lp + ql * T.cs, base + c * plane + (size_t)(P.line0 + r) * T.L + P.k0 + k,
-                 (uint32_t)(n * sizeof(C)), mbar);
-    }
-}
-
-// State shared by the two persistent passes: shared-memory arrays, the group
-// walk and the staging pipeline.
-struct PipeCtx {
-    float2* buf[2];
-    float2 *cf, *cb, *hf, *hb;
-    int S, ngroups, ncl, g;
-    bool stage, alive;
-};
-
-__device__ __forceinline__ PipeCtx pipe_setup(const PassArgsF& A, unsigned char* smem_raw, uint64_t* mbar,
-                                              uint64_t* cbar)
-{
-    const LineTiling& T = A.t;
-    PipeCtx X;
-    X.buf[0] = reinterpret_cast<float2*>(smem_raw);
-    X.buf[1] = reinterpret_cast<float2*>(smem_raw + T.off_b);
-    X.cf = reinterpret_cast<float2*>(smem_raw + T.off_cf);
-    X.cb = reinterpret_cast<float2*>(smem_raw + T.off_cb);
-    X.hf = X.cb + 3 * T.R * T.Qc;
-    X.hb = X.cb + 3 * T.R * (T.Qc + 1);
-    X.S = T.S;
-    X.ngroups = T.nlines / T.R;
-    X.ncl = gridDim.x / T.S;
-    X.g = blockIdx.x / T.S;
-    X.alive = true;
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        if (T.S > 1) {
-            mbar_init(&cbar[0], 3 * T.R);
-            mbar_init(&cbar[1], 3 * T.R);
-        }
-    }
-    if (T.S > 1) cluster_arrive_relaxed();  // start half of the cluster barrier
-    __syncthreads();                        // the mbarriers are initialised before any copy or wait
-    return X;
-}
-
-// Top of iteration `it` (group X.g): prefetch the next group, then wait for this
-// one.  Returns false if this group's data is unreliable (a wait gave up now or
-// earlier); the CTA then keeps every barrier and carry of the cluster but stores
-// nothing.
-template <typename C>
-__device__ __forceinline__ bool pipe_acquire(PipeCtx& X, const PassArgsT<C>& A, size_t plane, int it, bool last,
-                                             uint64_t* mbar)
-{
-    const LineTiling& T = A.t;
-    bool prefetched = false;
-    if (X.stage && X.alive && !last) {
-        issue_chunks(X.buf[(it + 1) & 1], A.in, plane, T, make_part(T, (X.g + X.ncl) * X.S), &mbar[(it + 1) & 1]);
-        prefetched = true;
-    }
-    if (!X.stage || !X.alive) return X.alive;
-    if (mbar_wait_bounded(&mbar[it & 1], A.err, kWaitTries, (it >> 1) & 1)) return true;
-    X.alive = false;
-    // no copy may still be writing shared memory when the CTA leaves
-    if (prefetched) mbar_wait_bounded(&mbar[(it + 1) & 1], nullptr, kWaitTries, ((it + 1) >> 1) & 1);
-    return false;
-}
-
-template <int MODE, int M>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap_pipe(M)) xpass_pipe(PassArgsF A)
-{
-    typedef float R;
-    typedef float2 C;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t mbar[2];
-    __shared__ uint64_t cbar[2];
-    const LineTiling& T = A.t;
-    PipeCtx X = pipe_setup(A, smem_raw, mbar, cbar);
-    const int nx = A.nx, ny = A.ny;
-    const size_t plane = (size_t)nx * ny;
-    // pointwise constants, rounded to FP32 once on the host (the pending scale
-    // converted once per thread)
-    const float s = (float)*A.scale;
-    PConstT<R> k;
-    k.dtc0 = A.kf[0] * s * s;
-    k.dtc2 = A.kf[1] * s * s;
-    k.dtr = A.kf[2];
-    k.s = s;
-    k.dt = A.kf[3];
-    const R fx0 = A.kf[4], fdx = A.kf[5], fy0 = A.kf[6], fdy = A.kf[7], hx = A.kf[8], hy = A.kf[9];
-    Part P = make_part(T, X.g * X.S);
-    const int nl = P.nl, Ll = P.len, k0 = P.k0, Lp = T.Lp;  // the same for every group of this CTA
-    const FastDiv div_len(Ll), div_nl(nl);
-    const SPos spos(T);
-    X.stage = T.bulk && Ll > 0;
-    if (X.stage && X.g < X.ngroups) issue_chunks(X.buf[0], A.in, plane, T, P, &mbar[0]);
-    for (int it = 0; X.g < X.ngroups; ++it, X.g += X.ncl) {
-        const bool last = X.g + X.ncl >= X.ngroups;
-        C* const sa = X.buf[it & 1];
-        ConvCoef<C> cc{};
-        if (A.do_solve) cc = load_conv(A.coef + (size_t)P.line0 * 3, P);
-        const bool ok = pipe_acquire(X, A, plane, it, last, mbar);
-        const int line0 = P.line0;
-        for (int e = threadIdx.x; e < nl * Ll; e += T.threads) {
-            const int r = div_len(e), kl = e - r * Ll, i = k0 + kl, j = line0 + r;
-            C* row = sa + r * 3 * Lp + spos(kl);
-            C a, b, c;
-            if (X.stage) {
-                a = row[0];
-                b = row[Lp];
-                c = row[2 * Lp];
-            } else {
-                const size_t o = (size_t)j * nx + i;
-                a = A.in[o];
-                b = A.in[plane + o];
-                c = A.in[2 * plane + o];
-            }
-            R ps;
-            if (A.do_p) {
-                // dt V joins the scalar exponent (no table loads)
-                const R xx = fma(R(i), fdx, fx0), yy = fma(R(j), fdy, fy0);
-                const R tv = fma(hx * xx, xx, hy * yy * yy);
-                pointwise<MODE>(a, b, c, mkc<C>(R(1), R(0)), tv, k, ps);
-            } else {
-                ps = k.s;
-            }
-            C p, z, m;
-            to_sigma_y(a, b, c, ps, p, z, m);
-            row[0] = p;
-            row[Lp] = z;
-            row[2 * Lp] = m;
-        }
-        __syncthreads();
-        if (A.do_solve)
-            chunked_thomas_reg<MODE, C, M>(sa, X.cf, X.cb, A.coef + (size_t)line0 * 3, cc, T, P, X.hf, X.hb, cbar, A.err,
-                                           it == 0, last, (uint32_t)(it & 1));
-        // transposed store t[mu][i][j], consecutive threads -> consecutive j
-        for (int e = threadIdx.x; e < nl * Ll; e += T.threads) {
-            const int kl = div_nl(e), r = e - kl * nl, i = k0 + kl, j = line0 + r;
-            const C* src = sa + r * 3 * Lp + spos(kl);
-            C xp, x0, xm;
-            sigma_y_to_x(src[0], src[Lp], src[2 * Lp], xp, x0, xm);
-            if (!ok) continue;
-            const size_t o = (size_t)i * ny + j;
-            A.out[o] = xp;
-            A.out[plane + o] = x0;
-            A.out[2 * plane + o] = xm;
-        }
-        fence_proxy_async_smem();  // these accesses to sa come before the copies that reuse it
-        __syncthreads();
-        P = make_part(T, (X.g + X.ncl) * X.S);
-    }
-    if (X.S > 1) cluster_wait();  // exit half: no neighbour store into this CTA is in flight
-}
-
-template <int MODE, int M>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap_pipe(M)) ypass_pipe(PassArgsF A)
-{
-    typedef float R;
-    typedef float2 C;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t mbar[2];
-    __shared__ uint64_t cbar[2];
-    __shared__ double wsum[32];
-    const LineTiling& T = A.t;
-    PipeCtx X = pipe_setup(A, smem_raw, mbar, cbar);
-    const int nx = A.nx, ny = A.ny;
-    const size_t plane = (size_t)nx * ny;
-    Part P = make_part(T, X.g * X.S);
-    const int nl = P.nl, Ll = P.len, k0 = P.k0, Lp = T.Lp;
-    const FastDiv div_len(Ll), div_nl(nl);
-    const SPos spos(T);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    X.stage = T.bulk && Ll > 0;
-    if (X.stage && X.g < X.ngroups) issue_chunks(X.buf[0], A.in, plane, T, P, &mbar[0]);
-    for (int it = 0; X.g < X.ngroups; ++it, X.g += X.ncl) {
-        const bool last = X.g + X.ncl >= X.ngroups;
-        C* const sa = X.buf[it & 1];
-        ConvCoef<C> cc{};
-        if (A.do_solve) cc = load_conv(A.coef + (size_t)P.line0 * 3, P);
-        const bool ok = pipe_acquire(X, A, plane, it, last, mbar);
-        const int line0 = P.line0;
-        if (!X.stage) {  // rows not 16-byte aligned: plain loads into the line array
-            for (int e = threadIdx.x; e < nl * Ll; e += T.threads) {
-                const int r = div_len(e), kl = e - r * Ll, j = k0 + kl, i = line0 + r;
-                C* dst = sa + r * 3 * Lp + spos(kl);
-                const size_t o = (size_t)i * ny + j;
-                dst[0] = A.in[o];
-                dst[Lp] = A.in[plane + o];
-                dst[2 * Lp] = A.in[2 * plane + o];
-            }
-        }
-        __syncthreads();
-        if (A.do_solve)
-            chunked_thomas_reg<MODE, C, M>(sa, X.cf, X.cb, A.coef + (size_t)line0 * 3, cc, T, P, X.hf, X.hb, cbar, A.err,
-                                           it == 0, last, (uint32_t)(it & 1));
-        R acc = R(0), acc3[3] = {R(0), R(0), R(0)};
-        for (int e = threadIdx.x; e < nl * Ll; e += T.threads) {
-            const int kl = div_nl(e), r = e - kl * nl, j = k0 + kl, i = line0 + r;
-            const C* src = sa + r * 3 * Lp + spos(kl);
-            C a, b, c;
-            from_sigma_x(src[0], src[Lp], src[2 * Lp], a, b, c);
-            if (!ok) continue;
-            const size_t o = (size_t)j * nx + i;
-            A.out[o] = a;
-            A.out[plane + o] = b;
-            A.out[2 * plane + o] = c;
-            if (A.mcomp) {
-                acc3[0] += fma(a.x, a.x, a.y * a.y);
-                acc3[1] += fma(b.x, b.x, b.y * b.y);
-                acc3[2] += fma(c.x, c.x, c.y * c.y);
-            } else {
-                acc += fma(a.x, a.x, a.y * a.y) + fma(b.x, b.x, b.y * b.y) + fma(c.x, c.x, c.y * c.y);
-            }
-        }
-        // partial norms of this group at the one-group pass's index (group * S + rank)
-        const int cta = X.g * X.S + P.rank;
-        if (A.partials && A.mcomp) {
-            for (int q = 0; q < 3; ++q) {
-                R racc = acc3[q];
-                for (int off = 16; off > 0; off >>= 1) racc += __shfl_xor_sync(0xffffffffu, racc, off);
-                if (lane == 0) wsum[warp] = (double)racc;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    double t = 0.0;
-                    for (int w = 0; w < nw; ++w) t += wsum[w];
-                    A.partials[3 * cta + q] = t;
-                }
-                __syncthreads();
-            }
-        } else if (A.partials) {
-            R racc = acc;
-            for (int off = 16; off > 0; off >>= 1) racc += __shfl_xor_sync(0xffffffffu, racc, off);
-            if (lane == 0) wsum[warp] = (double)racc;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double t = 0.0;
-                for (int w = 0; w < nw; ++w) t += wsum[w];
-                A.partials[cta] = t;
-            }
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
-        P = make_part(T, (X.g + X.ncl) * X.S);
-    }
-    if (X.S > 1) cluster_wait();
-}
-
 // ------------------------------------------------------------- launchers ---
 template <typename C>
 static int launch_coef_t(LineCoefT<C>* coef, int nlines, int dir, int mode, double h, double line_len,
@@ -1636,85 +1348,12 @@ static int launch_pass(K kernel, const A& a, cudaStream_t st)
     return report_cuda(cudaLaunchKernelEx(&cfg, kernel, a), "line pass cluster launch");
 }
 
-// Grid of a persistent pass: one cluster (or CTA) per resident slot, at most one
-// per line group.  The number of resident slots of a kernel and launch shape is
-// queried once and cached.
-template <typename K>
-static int launch_persistent(K kernel, const PassArgsF& a, cudaStream_t st)
-{
-    const LineTiling& t = a.t;
-    if (t.smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem);
-        if (e != cudaSuccess) return report_cuda(e, "cudaFuncSetAttribute(persistent pass)");
-    }
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return report_cuda(cudaGetLastError(), "cudaGetDevice");
-    struct Entry {
-        const void* k;
-        int dev, threads, S;
-        size_t smem;
-        int slots;
-    };
-    static std::mutex mu;
-    static std::vector<Entry> cache;
-    int slots = -1;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        for (const Entry& e : cache)
-            if (e.k == (const void*)kernel && e.dev == dev && e.threads == t.threads && e.S == t.S && e.smem == t.smem)
-                slots = e.slots;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.blockDim = dim3(t.threads);
-    cfg.dynamicSmemBytes = t.smem;
-    cfg.stream = st;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = t.S;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = t.S > 1 ? 1 : 0;
-    if (slots < 0) {
-        int n = 0;
-        if (t.S == 1) {
-            int nsm = 0, nb = 0;
-            if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, t.threads, t.smem) != cudaSuccess)
-                return report_cuda(cudaGetLastError(), "occupancy of a persistent pass");
-            n = nb * nsm;
-        } else {
-            cfg.gridDim = dim3(t.S);
-            if (cudaOccupancyMaxActiveClusters(&n, (const void*)kernel, &cfg) != cudaSuccess)
-                return report_cuda(cudaGetLastError(), "cluster occupancy of a persistent pass");
-        }
-        if (n < 1) return report_cuda(cudaErrorInvalidConfiguration, "persistent pass does not fit on an SM");
-        slots = n;
-        std::lock_guard<std::mutex> lock(mu);
-        cache.push_back(Entry{(const void*)kernel, dev, t.threads, t.S, t.smem, slots});
-    }
-    const int ngroups = t.nlines / t.R;
-    cfg.gridDim = dim3(std::min(ngroups, slots) * t.S);
-    return report_cuda(cudaLaunchKernelEx(&cfg, kernel, a), "persistent pass launch");
-}
-
 // Kernel for the tiling: a one-array complex64 tiling (m = 16, 24, 32) runs the
-// register-resident solve compiled for its m (in the persistent pipelined pass
-// when the tiling asks for it), every other tiling the shared-memory solve.
+// register-resident solve compiled for its m, every other tiling the
+// shared-memory solve.
 template <bool X, int MODE, typename C>
 static int launch_line_pass(const PassArgsT<C>& a, cudaStream_t st)
 {
-    if (a.t.single && a.t.persist) {
-        if constexpr (sizeof(C) == sizeof(float2)) {
-            switch (a.t.m) {
-            case 16: return X ? launch_persistent(xpass_pipe<MODE, 16>, a, st) : launch_persistent(ypass_pipe<MODE, 16>, a, st);
-            case 24: return X ? launch_persistent(xpass_pipe<MODE, 24>, a, st) : launch_persistent(ypass_pipe<MODE, 24>, a, st);
-            case 32: return X ? launch_persistent(xpass_pipe<MODE, 32>, a, st) : launch_persistent(ypass_pipe<MODE, 32>, a, st);
-            default: break;
-            }
-        }
-        return GP_ERR_ARG;
-    }
     if (a.t.single) {
         if constexpr (sizeof(C) == sizeof(float2)) {
             switch (a.t.m) {

@@ -160,7 +160,7 @@ def load():
     lib.gp_autotune.restype = ctypes.c_int
     lib.gp_tiling_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_tiling_info.restype = ctypes.c_int
-    lib.gp_set_tiling.argtypes = [vp, ip, ip, ip, ip, ip, ip]
+    lib.gp_set_tiling.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.gp_plan_tiling.argtypes = [ctypes.POINTER(Params), ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_plan_tiling.restype = ctypes.c_int
     lib.gp_set_tiling.restype = ctypes.c_int
@@ -252,8 +252,7 @@ def plan_tiling(params, mode=IMAG):
         v = (ctypes.c_int * 12)()
         _check(load().gp_plan_tiling(ctypes.byref(p), int(mode), d, v), "gp_plan_tiling")
         out[name] = dict(cluster=v[0], lines_per_cta=v[1], chunk=v[2], chunks=v[3], threads=v[4], smem=v[5],
-                         ctas=v[6], register_solve=bool(v[7]), pipelined=v[7] == 2, fixup=v[8],
-                         chunk_stride=v[9], line_stride=v[10],
+                         ctas=v[6], register_solve=bool(v[7]), fixup=v[8], chunk_stride=v[9], line_stride=v[10],
                          bank_conflicts=v[11])
     return out
 
@@ -376,11 +375,10 @@ class Solver:
         _check(load().gp_autotune(self._h, int(mode), ctypes.byref(ms)), "gp_autotune")
         return ms.value
 
-    def set_tiling(self, dir, cluster=1, lines_per_cta=1, chunk=0, mode=IMAG, pipelined=True):
-        """Force the tiling of the x-pass (dir 0) or y-pass (dir 1); pipelined
-        selects the persistent complex64 pass where the line count allows it."""
-        _check(load().gp_set_tiling(self._h, int(mode), int(dir), int(cluster), int(lines_per_cta), int(chunk),
-                                    int(bool(pipelined))), "gp_set_tiling")
+    def set_tiling(self, dir, cluster=1, lines_per_cta=1, chunk=0, mode=IMAG):
+        """Force the tiling of the x-pass (dir 0) or y-pass (dir 1)."""
+        _check(load().gp_set_tiling(self._h, int(mode), int(dir), int(cluster), int(lines_per_cta), int(chunk)),
+               "gp_set_tiling")
 
     def tiling(self, mode=IMAG):
         """Tiling of the x- and y-pass: dicts of cluster size, lines per CTA, chunk length..."""
@@ -389,7 +387,7 @@ class Solver:
             v = (ctypes.c_int * 8)()
             _check(load().gp_tiling_info(self._h, int(mode), d, v), "gp_tiling_info")
             out[name] = dict(cluster=v[0], lines_per_cta=v[1], chunk=v[2], chunks=v[3], threads=v[4], smem=v[5],
-                             ctas=v[6], register_solve=bool(v[7]), pipelined=v[7] == 2)
+                             ctas=v[6], register_solve=bool(v[7]))
         return out
 
     def checkpoint(self):

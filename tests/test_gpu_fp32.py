@@ -153,24 +153,3 @@ def test_fp32_full_size_precision2048_autotuned_step_parity():
         s.propagate(2, IMAG)
         got = s.get_state()
     assert np.max(np.abs(got - want)) <= 2e-6 * np.max(np.abs(want))
-
-
-@pytest.mark.parametrize("cluster,lines", [(1, 4), (2, 2), (4, 1), (8, 2)])
-def test_pipelined_passes_equal_one_group_passes_bitwise(cluster, lines):
-    """The persistent complex64 passes (one cluster per resident slot walking over
-    the line groups, the next group staged while the current one is computed)
-    give bitwise the results of the passes that run one line group per CTA."""
-    p = ragged(nx=640, ny=608, xlen=0.05 * 640, ylen=0.05 * 608, dt=0.0005)
-    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=12, phase_noise=0.3)
-    out = []
-    for pipelined in (True, False):
-        with gpspin.Solver(p) as s:
-            s.set_state(psi)
-            for d in (0, 1):
-                s.set_tiling(d, cluster=cluster, lines_per_cta=lines, chunk=24, pipelined=pipelined)
-            t = s.tiling()
-            assert t["xpass"]["pipelined"] == pipelined and t["ypass"]["pipelined"] == pipelined
-            for mode in (IMAG, REAL):
-                s.propagate(20, mode)  # crosses the 16-step graph block
-            out.append((s.get_state(), s.observables()["energy"]))
-    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
