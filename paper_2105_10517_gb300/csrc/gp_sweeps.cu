@@ -966,21 +966,8 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     const FastDiv div_len(Ll), div_nl(nl);
     const SPos spos(T);
     const int Lp = T.Lp;
-    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
-        int r = div_len(e), kl = e - r * Ll, i = k0 + kl, j = line0 + r;
-        C a, b, c;
-        if (T.bulk) {
-            const int ss = M > 0 ? Lp : Ll;
-            const C* row = M > 0 ? sa + r * 3 * Lp + spos(kl) : sb + (size_t)r * 3 * Ll + kl;
-            a = row[0];
-            b = row[ss];
-            c = row[2 * ss];
-        } else {
-            size_t o = (size_t)j * nx + i;
-            a = A.in[o];
-            b = A.in[plane + o];
-            c = A.in[2 * plane + o];
-        }
+    // P (when asked) and U_y^dagger of the site (i, j)
+    auto site = [&](C a, C b, C c, int i, int j, C& p, C& z, C& m) {
         R ps;
         if (A.do_p) {
             if constexpr (sizeof(R) == 8) {
@@ -996,8 +983,48 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         } else {
             ps = k.s;  // channels pass through, with the pending normalisation
         }
-        C p, z, m;
         to_sigma_y(a, b, c, ps, p, z, m);
+    };
+    bool paired = false;
+    if constexpr (M > 0) {
+        if (T.bulk) {
+            // Pairs of neighbouring sites (kl even): a chunk holds an even number of
+            // points and starts on a 16-byte boundary, so each component of the
+            // pair moves as one 16-byte access; the chunk index is a division by
+            // the compile-time chunk length.
+            paired = true;
+            const int Lh = Ll >> 1, pad = T.cs - M, q4 = Lp >> 1;
+            const FastDiv div_lh(Lh);
+            for (int q = threadIdx.x; threadIdx.x < T.threads && q < nl * Lh; q += T.threads) {
+                const int r = div_lh(q), kl = 2 * (q - r * Lh), i = k0 + kl, j = line0 + r;
+                float4* row = reinterpret_cast<float4*>(sa + r * 3 * Lp + kl + (kl / M) * pad);
+                const float4 va = row[0], vb = row[q4], vc = row[2 * q4];
+                C p0, z0, m0, p1, z1, m1;
+                site(mkc<C>(va.x, va.y), mkc<C>(vb.x, vb.y), mkc<C>(vc.x, vc.y), i, j, p0, z0, m0);
+                site(mkc<C>(va.z, va.w), mkc<C>(vb.z, vb.w), mkc<C>(vc.z, vc.w), i + 1, j, p1, z1, m1);
+                row[0] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                row[q4] = make_float4(z0.x, z0.y, z1.x, z1.y);
+                row[2 * q4] = make_float4(m0.x, m0.y, m1.x, m1.y);
+            }
+        }
+    }
+    for (int e = threadIdx.x; !paired && threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+        int r = div_len(e), kl = e - r * Ll, i = k0 + kl, j = line0 + r;
+        C a, b, c;
+        if (T.bulk) {
+            const int ss = M > 0 ? Lp : Ll;
+            const C* row = M > 0 ? sa + r * 3 * Lp + spos(kl) : sb + (size_t)r * 3 * Ll + kl;
+            a = row[0];
+            b = row[ss];
+            c = row[2 * ss];
+        } else {
+            size_t o = (size_t)j * nx + i;
+            a = A.in[o];
+            b = A.in[plane + o];
+            c = A.in[2 * plane + o];
+        }
+        C p, z, m;
+        site(a, b, c, i, j, p, z, m);
         C* dst = sa + r * 3 * Lp + spos(kl);
         dst[0] = p;
         dst[Lp] = z;
@@ -1041,7 +1068,30 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         return;
     }
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
-    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+    bool pstore = false;
+    if constexpr (M > 0) {
+        if (((nl | ny | line0) & 1) == 0) {
+            // lines j, j + 1 (j even) at the same i: one 16-byte store per channel
+            pstore = true;
+            const int nh = nl >> 1, pad = T.cs - M;
+            const size_t ph = plane >> 1;
+            const FastDiv div_nh(nh);
+            for (int q = threadIdx.x; threadIdx.x < T.threads && q < nh * Ll; q += T.threads) {
+                const int kl = div_nh(q), r = 2 * (q - kl * nh), i = k0 + kl, j = line0 + r;
+                const C* s0 = sa + r * 3 * Lp + kl + (kl / M) * pad;
+                const C* s1 = s0 + 3 * Lp;
+                C xp0, x00, xm0, xp1, x01, xm1;
+                sigma_y_to_x(s0[0], s0[Lp], s0[2 * Lp], xp0, x00, xm0);
+                sigma_y_to_x(s1[0], s1[Lp], s1[2 * Lp], xp1, x01, xm1);
+                if (!ok) continue;
+                float4* o = reinterpret_cast<float4*>(A.out + (size_t)i * ny + j);
+                o[0] = make_float4(xp0.x, xp0.y, xp1.x, xp1.y);
+                o[ph] = make_float4(x00.x, x00.y, x01.x, x01.y);
+                o[2 * ph] = make_float4(xm0.x, xm0.y, xm1.x, xm1.y);
+            }
+        }
+    }
+    for (int e = threadIdx.x; !pstore && threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, i = k0 + kl, j = line0 + r;
         C xp, x0, xm;
         const C* src = sa + r * 3 * Lp + spos(kl);
@@ -1182,7 +1232,41 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     __syncthreads();
     if (A.do_solve) solve_lines<MODE, C, M>(sa, sb, cf, cb, A.coef + (size_t)line0 * 3, cc, T, P, cbar, A.err);
     R acc = R(0), acc3[3] = {R(0), R(0), R(0)};
-    for (int e = threadIdx.x; threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
+    auto tally = [&](C a, C b, C c) {
+        if (A.mcomp) {
+            acc3[0] += fma(a.x, a.x, a.y * a.y);
+            acc3[1] += fma(b.x, b.x, b.y * b.y);
+            acc3[2] += fma(c.x, c.x, c.y * c.y);
+        } else {
+            acc += fma(a.x, a.x, a.y * a.y) + fma(b.x, b.x, b.y * b.y) + fma(c.x, c.x, c.y * c.y);
+        }
+    };
+    bool pstore = false;
+    if constexpr (M > 0) {
+        if (((nl | nx | line0) & 1) == 0) {
+            // columns i, i + 1 (i even) at the same j: one 16-byte store per component
+            pstore = true;
+            const int nh = nl >> 1, pad = T.cs - M;
+            const size_t ph = plane >> 1;
+            const FastDiv div_nh(nh);
+            for (int q = threadIdx.x; threadIdx.x < T.threads && q < nh * Ll; q += T.threads) {
+                const int kl = div_nh(q), r = 2 * (q - kl * nh), j = k0 + kl, i = line0 + r;
+                const C* s0 = sa + r * 3 * Lp + kl + (kl / M) * pad;
+                const C* s1 = s0 + 3 * Lp;
+                C a0, b0, c0, a1, b1, c1;
+                from_sigma_x(s0[0], s0[Lp], s0[2 * Lp], a0, b0, c0);
+                from_sigma_x(s1[0], s1[Lp], s1[2 * Lp], a1, b1, c1);
+                if (!ok) continue;
+                float4* o = reinterpret_cast<float4*>(A.out + (size_t)j * nx + i);
+                o[0] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                o[ph] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                o[2 * ph] = make_float4(c0.x, c0.y, c1.x, c1.y);
+                tally(a0, b0, c0);
+                tally(a1, b1, c1);
+            }
+        }
+    }
+    for (int e = threadIdx.x; !pstore && threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int kl = div_nl(e), r = e - kl * nl, j = k0 + kl, i = line0 + r;
         C a, b, c;
         const C* src = sa + r * 3 * Lp + spos(kl);
@@ -1192,13 +1276,7 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
         A.out[o] = a;
         A.out[plane + o] = b;
         A.out[2 * plane + o] = c;
-        if (A.mcomp) {
-            acc3[0] += fma(a.x, a.x, a.y * a.y);
-            acc3[1] += fma(b.x, b.x, b.y * b.y);
-            acc3[2] += fma(c.x, c.x, c.y * c.y);
-        } else {
-            acc += fma(a.x, a.x, a.y * a.y) + fma(b.x, b.x, b.y * b.y) + fma(c.x, c.x, c.y * c.y);
-        }
+        tally(a, b, c);
     }
     if (A.partials && A.mcomp) {
         // per-component partials (magnetisation-constrained normalisation)
