@@ -111,6 +111,11 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-plain", action="store_true", help="serving: skip the one-at-a-time FP64 baseline")
     ap.add_argument("--no-autotune", action="store_true", help="time the default tiling instead of the tuned one")
+    ap.add_argument("--tiling", default=None,
+                    help="S,R,m: cluster size, lines per CTA and chunk length of both passes (instead of autotuning)")
+    ap.add_argument("--substeps", action="store_true",
+                    help="time split of the passes: the x- and y-pass with only P, only the X solve, only the Y "
+                         "solve, then one full step (NVTX range 'substeps'); prints one JSON line")
     ap.add_argument("--splitting", default="lie", choices=["lie", "strang"],
                     help="lie: the first-order step (default); strang: the second-order extension (fp64)")
     ap.add_argument("--magnetization", type=float, default=None,
@@ -299,8 +304,62 @@ def prepare(name, prec, stream, args, main=True):
         s.set_splitting(gpspin.SPLIT_STRANG)
     if main and args.magnetization is not None:
         s.set_magnetization(args.magnetization)
-    tuned_ms = None if args.no_autotune else s.autotune(mode)  # the state is unchanged
+    tuned_ms = None
+    if args.tiling:
+        S, R, m = (int(v) for v in args.tiling.split(","))
+        for d in (0, 1):
+            s.set_tiling(d, cluster=S, lines_per_cta=R, chunk=m, mode=mode)
+    elif not args.no_autotune:
+        tuned_ms = s.autotune(mode)  # the state is unchanged
     return s, c, p, mode, prep_steps, tuned_ms
+
+
+def run_substeps(args):
+    """Device time of the pass pair with only P, only the X solve or only the Y
+    solve applied (gp_apply_substep), and of one full step (gp_profile_step): the
+    split of a step between data movement, the pointwise substep and the solves.
+    Each is the median of 30 launches after 3 warm-up ones, timed with CUDA
+    events on the handle's stream; then one of each runs inside the NVTX range
+    'substeps' for profilers."""
+    import torch
+    from paper_2105_10517_gb300 import gpspin
+    gpspin.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    name = args.workload
+    prec = args.precision or ("fp32" if name == "precision2048" else "fp64")
+    stream = torch.cuda.Stream()
+    s, c, p, mode, _, _ = prepare(name, prec, stream.cuda_stream, args)
+    s.apply_substep("P", mode)  # applies a pending normalisation once
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def med(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(30):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    out = {w: med(lambda: s.apply_substep(w, mode)) for w in ("P", "X", "Y")}
+    prof = [s.profile_step(mode) for _ in range(30)]
+    out["x_full"] = statistics.median(q[0] for q in prof)
+    out["y_full"] = statistics.median(q[1] for q in prof)
+    out["step"] = statistics.median(q[3] for q in prof)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("substeps")
+    for w in ("P", "X", "Y"):
+        s.apply_substep(w, mode)
+    s.profile_step(mode)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    tiles = s.tiling(mode)
+    s.close()
+    return {"mode": "substeps", "workload": name, "storage": prec, "unit": "ms", "substep_ms": out, "tiles": tiles,
+            "note": "P/X/Y: the x-pass and y-pass with only that substep applied (the others pass through)"}
 
 
 def timed_steps(s, mode, steps, warmup, stream, flush, barrier, clocks=None):
@@ -551,23 +610,47 @@ def run_serving(args):
         plain, rp = serve.serve_one_at_a_time(trace, cap=args.cap, tol=args.tol)
     clocks.stop()
 
+    ref = {r["arrival"]: r for r in rp}
+
+    def rel_de(r):
+        q = ref[r["arrival"]]
+        return abs(r["energy"] - q["energy"]) / abs(q["energy"])
+
     def agreement(ra):
-        ref = {r["arrival"]: r for r in rp}
         d_conv, d_cap = [], []
         for r in ra:
             q = ref[r["arrival"]]
-            d = abs(r["energy"] - q["energy"]) / abs(q["energy"])
-            (d_cap if (r["steps"] >= args.cap or q["steps"] >= args.cap) else d_conv).append(d)
+            (d_cap if (r["steps"] >= args.cap or q["steps"] >= args.cap) else d_conv).append(rel_de(r))
         f = lambda v: {"n": len(v), "max_rel_dE": max(v) if v else None,
                        "frac_within_1e-6": (sum(x <= 1e-6 for x in v) / len(v)) if v else None}
         return {"converged": f(d_conv), "capped": f(d_cap)}
 
+    def at_bar(summary, ra, tol=1e-6):
+        """Solves/s and p50/p99 counting only results within |dE/E| <= tol of the
+        plain FP64 result of the same request (the metric's accuracy bar)."""
+        ok = [r for r in ra if r["state"] == gpspin.REQ_DONE and rel_de(r) <= tol]
+        lat = [r["latency"] for r in ok]
+        pct = lambda q: float(np.percentile(lat, q)) if lat else None
+        return {"solves": len(ok), "solves_per_s": len(ok) / summary["makespan_s"], "p50_s": pct(50),
+                "p99_s": pct(99), "tol_rel_dE": tol}
+
+    paths = {"batched_mixed": (mixed, rm), "batched_fp64": (b64, rb), "plain_fp64_one_at_a_time": (plain, rp)}
+    bar = {k: at_bar(v[0], v[1]) for k, v in paths.items()}
+    best = max(("batched_mixed", "batched_fp64"), key=lambda k: bar[k]["solves_per_s"])
+    capped = sum(1 for r in rp if r["steps"] >= args.cap)
     return {
-        "metric": METRIC, "mode": "serving", "value": mixed["solves_per_s"], "unit": "solves/s",
-        "higher_is_better": True, "n_gpus": 1, "dtype": "f32 storage + f64 refinement",
+        "metric": METRIC, "mode": "serving", "value": bar[best]["solves_per_s"], "unit": "solves/s",
+        "value_path": best, "value_definition": "solves/s counting only results within |dE/E| <= 1e-6 of the "
+                                                "plain one-at-a-time FP64 result of the same request",
+        "higher_is_better": True, "n_gpus": 1,
+        "dtype": "f32 storage + f64 refinement" if best == "batched_mixed" else "f64",
         "data": f"synthetic request trace: {args.requests} requests, Poisson arrivals at {args.rate}/s (seed 4), "
                 f"N in {{128,256,384,512}}, DX=32/N, DT=0.1 DX^2, imaginary time to |dE|<{args.tol:g} per 100 "
                 f"steps, cap {args.cap}",
+        "plain_requests_at_cap": capped,
+        "at_1e-6": bar,
+        "speedup_at_1e-6_vs_plain": {k: bar[k]["solves_per_s"] / bar["plain_fp64_one_at_a_time"]["solves_per_s"]
+                                     for k in ("batched_mixed", "batched_fp64")},
         "batched_mixed": mixed, "batched_fp64": b64, "plain_fp64_one_at_a_time": plain,
         "speedup_solves_per_s_vs_plain": mixed["solves_per_s"] / plain["solves_per_s"],
         "speedup_fp64_batched_vs_plain": b64["solves_per_s"] / plain["solves_per_s"],
@@ -578,6 +661,9 @@ def run_serving(args):
 
 def main():
     args = parse()
+    if args.substeps:
+        print(json.dumps(run_substeps(args)))
+        return
     if args.serve:
         print(json.dumps(run_serving(args)))
         return
