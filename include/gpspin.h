@@ -301,21 +301,6 @@ int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_ct
  * (complex64, chunk length 16, 24 or 32).  out must hold 8 ints. */
 int gp_tiling_info(gp_handle* h, int mode, int dir, int* out);
 
-/* Whether the autotuner split a pass (dir 0: x-pass, 1: y-pass) into two
- * launches because the last wave of its tiling would leave part of the GPU idle:
- * out[0] the lines of the first launch, which fills whole waves (0: one launch),
- * out[1] CTAs per line group, out[2] lines per CTA, out[3] chunk length and
- * out[4] CTAs of the second launch, which runs the remaining lines with a finer
- * tiling.  Results stay within the parity tolerances.  out must hold 5 ints. */
-int gp_tiling_split(gp_handle* h, int mode, int dir, int* out);
-
-/* Splits a pass by hand as the autotuner may: the first first_lines lines (a
- * multiple of the pass's lines per CTA, and even) in one launch with the pass's
- * tiling, the rest in a second launch of `cluster` CTAs per line group and
- * lines_per_cta lines per CTA (same chunk length).  first_lines = 0 removes the
- * split.  GP_ERR_ARG or GP_ERR_UNSUPPORTED if either part does not fit. */
-int gp_set_split(gp_handle* h, int mode, int dir, int first_lines, int cluster, int lines_per_cta);
-
 /* The default tiling of a pass (dir 0: x-pass, 1: y-pass) for these parameters
  * and mode, the one a handle starts with, computed on the host without a
  * device: out[0..7] as gp_tiling_info, then out[8] the fixup length F (rows

@@ -174,7 +174,6 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
     t->off_cf = line_bytes * (single ? 1 : 2);
     t->off_cb = t->off_cf + up(3 * R * Qc * elem);
     t->bulk = 0;  // set per pass by the caller (needs 16-byte aligned rows)
-    t->split = 0;
     t->single = single ? 1 : 0;
     return GP_OK;
 }
@@ -305,7 +304,6 @@ int ensure_coef(gp_handle* h, int mode)
     cs.ty = ty;
     cs.ftx = ftx;
     cs.fty = fty;
-    cs.rx = cs.ry = cs.frx = cs.fry = LineTiling{};
     cs.ux = ux;
     cs.uy = uy;
     cs.fux = fux;
@@ -438,61 +436,6 @@ int sync_status(gp_handle* h)
 
 int y_blocks(const LineTiling& t) { return (t.nlines + t.R - 1) / t.R * t.S; }
 
-int y_parts(const LineTiling& t, const LineTiling& rest)
-{
-    if (t.split <= 0 || t.split >= t.nlines) return y_blocks(t);
-    LineTiling first = t;
-    first.nlines = t.split;
-    return y_blocks(first) + y_blocks(rest);
-}
-
-// The second launch of a split pass works on lines split .. nlines - 1 through
-// offset pointers: rows of psi and entries of t for the x-pass (lines are rows
-// j), rows of t and columns of psi for the y-pass (lines are columns i); the
-// per-line tables and the y coordinates of the x-pass's trap factor move with
-// them, and the y-pass's partial norms follow the first launch's.
-template <typename C>
-static int launch_split_t(const PassArgsT<C>& a, int dir, int mode, const LineTiling& rest, cudaStream_t st)
-{
-    auto launch = [&](const PassArgsT<C>& x) { return dir == 0 ? launch_xpass(x, mode, st) : launch_ypass(x, mode, st); };
-    const int sp = a.t.split;
-    if (sp <= 0 || sp >= a.t.nlines) return launch(a);
-    PassArgsT<C> a1 = a;
-    a1.t.nlines = sp;
-    int rc = launch(a1);
-    if (rc) return rc;
-    PassArgsT<C> a2 = a;
-    a2.t = rest;
-    a2.t.bulk = a.t.bulk;
-    a2.coef = a.coef + 3 * (size_t)sp;
-    a2.out = a.out + sp;
-    if (dir == 0) {
-        a2.in = a.in + (size_t)sp * a.nx;
-        a2.ey = a.ey + sp;
-        a2.y0 = a.y0 + sp * a.dy;
-        a2.kf[6] = (float)a2.y0;
-    } else {
-        a2.in = a.in + (size_t)sp * a.ny;
-        if (a.partials) a2.partials = a.partials + (size_t)y_blocks(a1.t) * (a.mcomp ? 3 : 1);
-    }
-    return launch(a2);
-}
-
-int launch_split(const PassArgs& a, int dir, int mode, const LineTiling& rest, cudaStream_t st)
-{
-    return launch_split_t(a, dir, mode, rest, st);
-}
-
-int launch_split(const PassArgsF& a, int dir, int mode, const LineTiling& rest, cudaStream_t st)
-{
-    return launch_split_t(a, dir, mode, rest, st);
-}
-
-static const LineTiling& rest_of(const CoefSet& cs, bool f32, int dir)
-{
-    return f32 ? (dir == 0 ? cs.frx : cs.fry) : (dir == 0 ? cs.rx : cs.ry);
-}
-
 size_t handle_bytes(const gp_params& p)
 {
     const size_t n = 3 * (size_t)p.nx * p.ny, lines = (size_t)p.nx + p.ny;
@@ -514,12 +457,9 @@ int apply_sigma(gp_handle* h, const PassArgsT<C>& ay)
 template <typename A>
 int enqueue_steps(gp_handle* h, int mode, const A& ax, const A& ay, int gy, long long n)
 {
-    const bool f32 = sizeof(*ax.in) == sizeof(float2);
-    const LineTiling& rx = rest_of(h->coef[mode], f32, 0);
-    const LineTiling& ry = rest_of(h->coef[mode], f32, 1);
     for (long long s = 0; s < n; ++s) {
-        LK(launch_split(ax, 0, mode, rx, h->stream));
-        LK(launch_split(ay, 1, mode, ry, h->stream));
+        LK(launch_xpass(ax, mode, h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
         if (mode == GP_IMAG && h->mcon) {
             // magnetisation-constrained normalisation, applied at once
             LK(launch_finalize_m(h->partials, gy, cell(h), h->m_target, h->scal + 3, h->flag, h->stream));
@@ -651,7 +591,7 @@ int propagate_active(gp_handle* h, long long nsteps, int mode)
     const CoefSet& cs = h->coef[mode];
     if (mode == GP_REAL && (st = flush_scale(h))) return st;
     const bool f32 = h->active == GP_FP32_MIXED;
-    const int gy = f32 ? y_parts(cs.fty, cs.fry) : y_parts(cs.ty, cs.ry);
+    const int gy = y_blocks(f32 ? cs.fty : cs.ty);
     const bool mc = mode == GP_IMAG && h->mcon;
     if (gy * (mc ? 3 : 1) > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
     if (mc) {
@@ -928,7 +868,7 @@ int gp_propagate_host(gp_handle* h, const double* psi_in, long long nsteps, int 
     int st = ensure_coef(h, mode);
     if (st) return st;
     const CoefSet& cs = h->coef[mode];
-    const int gy = y_parts(cs.ty, cs.ry);
+    const int gy = y_blocks(cs.ty);
     if (gy * (mc ? 3 : 1) > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
     if (mc && (gamma_of(h->p) != 0.0 || h->p.rabi != 0.0)) return GP_ERR_ARG;
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
@@ -981,16 +921,16 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out)
         if (mc && (gamma_of(h->p) != 0.0 || h->p.rabi != 0.0)) return GP_ERR_ARG;
         if ((mode == GP_REAL || mc) && (st = flush_scale(h))) return st;
         const bool f32 = h->active == GP_FP32_MIXED;
-        const int gy = f32 ? y_parts(cs.fty, cs.fry) : y_parts(cs.ty, cs.ry);
+        const int gy = y_blocks(f32 ? cs.fty : cs.ty);
         if (gy * (mc ? 3 : 1) > kNormBlocksMax) return GP_ERR_UNSUPPORTED;
         CK(cudaEventRecord(h->ev[0], h->stream));
         if (f32) {
             PassArgsF ax = pass_args_f32(h, cs, 0), ay = pass_args_f32(h, cs, 1);
             if (mode == GP_IMAG) ay.partials = h->partials;
             ay.mcomp = mc;
-            LK(launch_split(ax, 0, mode, cs.frx, h->stream));
+            LK(launch_xpass(ax, mode, h->stream));
             CK(cudaEventRecord(h->ev[1], h->stream));
-            LK(launch_split(ay, 1, mode, cs.fry, h->stream));
+            LK(launch_ypass(ay, mode, h->stream));
             CK(cudaEventRecord(h->ev[2], h->stream));
             CK(cudaEventRecord(h->ev[3], h->stream));
             if (mc) {
@@ -1001,9 +941,9 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out)
             PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
             if (mode == GP_IMAG) ay.partials = h->partials;
             ay.mcomp = mc;
-            LK(launch_split(ax, 0, mode, cs.rx, h->stream));
+            LK(launch_xpass(ax, mode, h->stream));
             CK(cudaEventRecord(h->ev[1], h->stream));
-            LK(launch_split(ay, 1, mode, cs.ry, h->stream));
+            LK(launch_ypass(ay, mode, h->stream));
             CK(cudaEventRecord(h->ev[2], h->stream));
             CK(cudaEventRecord(h->ev[3], h->stream));
             if (mc) {
@@ -1031,25 +971,16 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out)
 }
 
 extern "C++" {
-template <typename A>
-A with_tiling(A a, const LineTiling& t)
-{
-    const int bulk = a.t.bulk;
-    a.t = t;
-    a.t.bulk = bulk;
-    return a;
-}
-
 // Times one pass (x: dir 0, y: dir 1) with the given tiling: best of three
 // launches on the handle's stream, in ms (negative if the launch fails).
 template <typename A>
-float time_pass(gp_handle* h, A a, int dir, int mode, const LineTiling& rest)
+float time_pass(gp_handle* h, A a, int dir, int mode)
 {
     a.partials = nullptr;
     float best = -1.0f;
     for (int rep = 0; rep < 4; ++rep) {
         if (cudaEventRecord(h->ev[0], h->stream) != cudaSuccess) return -1.0f;
-        int rc = launch_split(a, dir, mode, rest, h->stream);
+        int rc = dir == 0 ? launch_xpass(a, mode, h->stream) : launch_ypass(a, mode, h->stream);
         if (rc || cudaEventRecord(h->ev[1], h->stream) != cudaSuccess || cudaEventSynchronize(h->ev[1]) != cudaSuccess)
             return -1.0f;
         float ms = 0;
@@ -1086,21 +1017,7 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
         const double cp = max_cp(p, dir, mode);
         LineTiling& cur = f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty);
         LineTiling best = cur;
-        best.split = 0;
         float best_ms = -1.0f;
-        // device time of the pass with tiling t (and second launch r when t is split)
-        auto time_tiling = [&](LineTiling t, const LineTiling& r) {
-            if (f32) {
-                PassArgsF a = pass_args_f32(h, cs, dir);
-                t.bulk = a.t.bulk;
-                a.t = t;
-                return time_pass(h, a, dir, mode, r);
-            }
-            PassArgs a = pass_args(h, cs, dir);
-            t.bulk = a.t.bulk;
-            a.t = t;
-            return time_pass(h, a, dir, mode, r);
-        };
         const int ms_add[] = {0, 4, 8, 16, 32};
         for (int S : {1, 2, 4, 8})
             for (int R : {1, 2, 4, 8})
@@ -1110,44 +1027,26 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
                         GP_OK)
                         continue;
                     if (S > 1 && L < 64) continue;
-                    const float ms = time_tiling(t, LineTiling{});
+                    float ms;
+                    if (f32) {
+                        PassArgsF a = pass_args_f32(h, cs, dir);
+                        t.bulk = a.t.bulk;
+                        a.t = t;
+                        ms = time_pass(h, a, dir, mode);
+                    } else {
+                        PassArgs a = pass_args(h, cs, dir);
+                        t.bulk = a.t.bulk;
+                        a.t = t;
+                        ms = time_pass(h, a, dir, mode);
+                    }
                     if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
                         best_ms = ms;
                         best = t;
                     }
                 }
         if (best_ms < 0) st = GP_ERR_CUDA;
-        // When the last wave of the best tiling is only partly full, try running
-        // the whole waves as one launch and the remaining lines as a second launch
-        // with a finer tiling; keep the split if it measures faster.
-        LineTiling best_rest{};
-        const int slots = st ? -1 : (f32 ? pass_slots(with_tiling(pass_args_f32(h, cs, dir), best), dir, mode)
-                                         : pass_slots(with_tiling(pass_args(h, cs, dir), best), dir, mode));
-        const int groups = (nl + best.R - 1) / best.R;
-        if (slots > 0 && groups > slots && groups % slots != 0) {
-            const int split = groups / slots * slots * best.R;
-            if (split % 2 == 0 && split < nl) {
-                for (int S : {1, 2, 4, 8})
-                    for (int R : {1, 2, 4}) {
-                        LineTiling r;
-                        if (make_tiling(L, nl - split, cp, f32 ? TILE_C64_REG : TILE_C128, S, R, best.m, &r) != GP_OK)
-                            continue;
-                        if (S > 1 && L < 64) continue;
-                        LineTiling t = best;
-                        t.split = split;
-                        const float ms = time_tiling(t, r);
-                        if (ms > 0 && ms < best_ms) {
-                            best_ms = ms;
-                            best = t;
-                            best_rest = r;
-                        }
-                    }
-            }
-        }
-        cudaGetLastError();
         cur = best;
         cur.bulk = 0;
-        (f32 ? (dir == 0 ? cs.frx : cs.fry) : (dir == 0 ? cs.rx : cs.ry)) = best_rest;
         best_total += best_ms;
     }
     cudaGetLastError();
@@ -1197,56 +1096,7 @@ int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_ct
                      f32 ? TILE_C64_REG : TILE_C128, cluster, lines_per_cta, chunk, &t);
     if (st) return st;
     (f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty)) = t;
-    (f32 ? (dir == 0 ? cs.frx : cs.fry) : (dir == 0 ? cs.rx : cs.ry)) = LineTiling{};
     drop_graphs(h);
-    return GP_OK;
-}
-
-int gp_set_split(gp_handle* h, int mode, int dir, int first_lines, int cluster, int lines_per_cta)
-{
-    if (!h || (mode != GP_IMAG && mode != GP_REAL) || dir < 0 || dir > 1) return GP_ERR_ARG;
-    int st = ensure_coef(h, mode);
-    if (st) return st;
-    CoefSet& cs = h->coef[mode];
-    const gp_params& p = h->p;
-    const bool f32 = h->active == GP_FP32_MIXED;
-    LineTiling& t = f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty);
-    LineTiling& r = f32 ? (dir == 0 ? cs.frx : cs.fry) : (dir == 0 ? cs.rx : cs.ry);
-    if (first_lines == 0) {
-        t.split = 0;
-        r = LineTiling{};
-        drop_graphs(h);
-        return GP_OK;
-    }
-    // the first launch covers whole line groups and keeps 16-byte alignment of
-    // the second launch's offset pointers
-    if (first_lines < 0 || first_lines >= t.nlines || first_lines % t.R || first_lines % 2) return GP_ERR_ARG;
-    LineTiling rest;
-    st = make_tiling(dir == 0 ? p.nx : p.ny, t.nlines - first_lines, max_cp(p, dir, mode),
-                     f32 ? TILE_C64_REG : TILE_C128, cluster, lines_per_cta, t.m, &rest);
-    if (st) return st;
-    if (rest.m != t.m) return GP_ERR_ARG;
-    t.split = first_lines;
-    r = rest;
-    drop_graphs(h);
-    return GP_OK;
-}
-
-int gp_tiling_split(gp_handle* h, int mode, int dir, int* out)
-{
-    if (!h || !out || (mode != GP_IMAG && mode != GP_REAL) || dir < 0 || dir > 1) return GP_ERR_ARG;
-    int st = ensure_coef(h, mode);
-    if (st) return st;
-    const CoefSet& cs = h->coef[mode];
-    const bool f32 = h->active == GP_FP32_MIXED;
-    const LineTiling& t = f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty);
-    const LineTiling& r = rest_of(cs, f32, dir);
-    const bool on = t.split > 0 && t.split < t.nlines;
-    out[0] = on ? t.split : 0;
-    out[1] = on ? r.S : 0;
-    out[2] = on ? r.R : 0;
-    out[3] = on ? r.m : 0;
-    out[4] = on ? y_blocks(r) : 0;
     return GP_OK;
 }
 
@@ -1281,15 +1131,15 @@ int gp_apply_substep(gp_handle* h, int which, int mode)
         ax.do_p = which == 0;
         ax.do_solve = which == 1;
         ay.do_solve = which == 2;
-        LK(launch_split(ax, 0, mode, cs.frx, h->stream));
-        LK(launch_split(ay, 1, mode, cs.fry, h->stream));
+        LK(launch_xpass(ax, mode, h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
     } else {
         PassArgs ax = pass_args(h, cs, 0), ay = pass_args(h, cs, 1);
         ax.do_p = which == 0;
         ax.do_solve = which == 1;
         ay.do_solve = which == 2;
-        LK(launch_split(ax, 0, mode, cs.rx, h->stream));
-        LK(launch_split(ay, 1, mode, cs.ry, h->stream));
+        LK(launch_xpass(ax, mode, h->stream));
+        LK(launch_ypass(ay, mode, h->stream));
     }
     return sync_status(h);
 }

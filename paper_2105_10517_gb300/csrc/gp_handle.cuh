@@ -20,7 +20,6 @@ struct CoefSet {
     float2* fex = nullptr;
     float2* fey = nullptr;
     LineTiling tx{}, ty{}, ftx{}, fty{};  // single-instance launches (may span 2-CTA clusters)
-    LineTiling rx{}, ry{}, frx{}, fry{};  // the second launch of a split pass (the lines past t.split)
     LineTiling ux{}, uy{}, fux{}, fuy{};  // unsplit, for batched launches
     // second-order splitting (complex128): x-pass tables and trap factors of dt/2
     bool half_valid = false;
@@ -74,12 +73,6 @@ PassArgsF pass_args_f32(gp_handle* h, const CoefSet& cs, int dir);
 size_t n_elems(const gp_handle* h);
 double cell(const gp_handle* h);
 int y_blocks(const LineTiling& t);
-// Partial norms a y-pass with this tiling (and this second launch, if split) writes.
-int y_parts(const LineTiling& t, const LineTiling& rest);
-// A pass as one launch, or, for a split tiling, as two: the first t.split lines,
-// then the rest with the tiling `rest` (pointers and coordinates offset).
-int launch_split(const PassArgs& a, int dir, int mode, const LineTiling& rest, cudaStream_t st);
-int launch_split(const PassArgsF& a, int dir, int mode, const LineTiling& rest, cudaStream_t st);
 int flush_scale(gp_handle* h);
 // Bytes of device memory gp_create allocates for these parameters, plus the
 // coefficient tables of one mode.

@@ -73,8 +73,6 @@ struct LineTiling {
     size_t off_cb;
     int bulk;      // rows are 16-byte aligned: stage them with cp.async.bulk
     int single;    // one line array: rows are staged in place (complex64 register-resident solve, m = 16/24/32)
-    int split;     // host side: 0, or the lines of a first launch that fills whole waves of the GPU; the
-                   // remaining lines run in a second launch with a finer tiling of their own
 };
 
 // Kinds of tiling: complex128; complex64 with the shared-memory solve (two line
@@ -120,10 +118,6 @@ int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int kind = TIL
 // CTA, chunk length m (raised to the minimum the precision needs).
 int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m, LineTiling* t);
 
-// Line groups (CTAs, or clusters of CTAs) of a pass that the GPU holds at once
-// with this tiling (occupancy of the kernel the tiling selects); < 0 on error.
-int pass_slots(const PassArgs& a, int dir, int mode);
-int pass_slots(const PassArgsF& a, int dir, int mode);
 // launchers (gp_sweeps.cu)
 int launch_coef(LineCoef* coef, int nlines, int dir, int mode, double h, double line_len, double line_h,
                 double dt, double omeg, double gamma, int eta, int* status, cudaStream_t st);

@@ -1446,66 +1446,6 @@ static int launch_line_pass(const PassArgsT<C>& a, cudaStream_t st)
     return X ? launch_pass(xpass_kernel<MODE, C>, a, st) : launch_pass(ypass_kernel<MODE, C>, a, st);
 }
 
-// Resident line groups of the kernel the tiling selects.
-template <typename K>
-static int slots_of(K kernel, const LineTiling& t)
-{
-    if (t.smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)t.smem) != cudaSuccess)
-        return -1;
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
-    if (t.S == 1) {
-        int nsm = 0;
-        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, t.threads, t.smem) != cudaSuccess)
-            return -1;
-        return n * nsm;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3(t.S);
-    cfg.blockDim = dim3(t.threads);
-    cfg.dynamicSmemBytes = t.smem;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = t.S;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&n, (const void*)kernel, &cfg) != cudaSuccess) return -1;
-    return n;
-}
-
-template <bool X, int MODE, typename C>
-static int pass_slots_t(const PassArgsT<C>& a)
-{
-    if (a.t.single) {
-        if constexpr (sizeof(C) == sizeof(float2)) {
-            switch (a.t.m) {
-            case 16: return X ? slots_of(xpass_kernel_reg<MODE, C, 16>, a.t) : slots_of(ypass_kernel_reg<MODE, C, 16>, a.t);
-            case 24: return X ? slots_of(xpass_kernel_reg<MODE, C, 24>, a.t) : slots_of(ypass_kernel_reg<MODE, C, 24>, a.t);
-            case 32: return X ? slots_of(xpass_kernel_reg<MODE, C, 32>, a.t) : slots_of(ypass_kernel_reg<MODE, C, 32>, a.t);
-            default: break;
-            }
-        }
-        return -1;
-    }
-    return X ? slots_of(xpass_kernel<MODE, C>, a.t) : slots_of(ypass_kernel<MODE, C>, a.t);
-}
-
-int pass_slots(const PassArgs& a, int dir, int mode)
-{
-    if (dir == 0) return mode == 1 ? pass_slots_t<true, 1>(a) : pass_slots_t<true, 0>(a);
-    return mode == 1 ? pass_slots_t<false, 1>(a) : pass_slots_t<false, 0>(a);
-}
-
-int pass_slots(const PassArgsF& a, int dir, int mode)
-{
-    if (dir == 0) return mode == 1 ? pass_slots_t<true, 1>(a) : pass_slots_t<true, 0>(a);
-    return mode == 1 ? pass_slots_t<false, 1>(a) : pass_slots_t<false, 0>(a);
-}
-
 int launch_xtail(const PassArgs& a, int mode, cudaStream_t st)
 {
     return mode == 1 ? launch_pass(xtail_kernel<1>, a, st) : launch_pass(xtail_kernel<0>, a, st);

@@ -34,7 +34,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
            "gp_init_winding", "gp_set_magnetization", "gp_set_splitting", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
-           "gp_tiling_info", "gp_tiling_split", "gp_set_split", "gp_set_tiling", "gp_plan_tiling", "gp_check_wait_timeout",
+           "gp_tiling_info", "gp_set_tiling", "gp_plan_tiling", "gp_check_wait_timeout",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_batch_use_graphs", "gp_batch_set_queue_limit", "gp_batch_cancel", "gp_batch_error",
            "gp_inject_alloc_failure", "gp_checkpoint_bytes", "gp_checkpoint_save", "gp_checkpoint_load",
@@ -160,10 +160,6 @@ def load():
     lib.gp_autotune.restype = ctypes.c_int
     lib.gp_tiling_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_tiling_info.restype = ctypes.c_int
-    lib.gp_tiling_split.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
-    lib.gp_tiling_split.restype = ctypes.c_int
-    lib.gp_set_split.argtypes = [vp, ip, ip, ip, ip, ip]
-    lib.gp_set_split.restype = ctypes.c_int
     lib.gp_set_tiling.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.gp_plan_tiling.argtypes = [ctypes.POINTER(Params), ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_plan_tiling.restype = ctypes.c_int
@@ -384,12 +380,6 @@ class Solver:
         _check(load().gp_set_tiling(self._h, int(mode), int(dir), int(cluster), int(lines_per_cta), int(chunk)),
                "gp_set_tiling")
 
-    def set_split(self, dir, first_lines, cluster=1, lines_per_cta=1, mode=IMAG):
-        """Run the first first_lines lines of a pass in one launch and the rest in a
-        second launch with this cluster size and lines per CTA (0: one launch)."""
-        _check(load().gp_set_split(self._h, int(mode), int(dir), int(first_lines), int(cluster), int(lines_per_cta)),
-               "gp_set_split")
-
     def tiling(self, mode=IMAG):
         """Tiling of the x- and y-pass: dicts of cluster size, lines per CTA, chunk length..."""
         out = {}
@@ -398,10 +388,6 @@ class Solver:
             _check(load().gp_tiling_info(self._h, int(mode), d, v), "gp_tiling_info")
             out[name] = dict(cluster=v[0], lines_per_cta=v[1], chunk=v[2], chunks=v[3], threads=v[4], smem=v[5],
                              ctas=v[6], register_solve=bool(v[7]))
-            w = (ctypes.c_int * 5)()
-            _check(load().gp_tiling_split(self._h, int(mode), d, w), "gp_tiling_split")
-            if w[0]:
-                out[name]["split"] = dict(first_lines=w[0], cluster=w[1], lines_per_cta=w[2], chunk=w[3], ctas=w[4])
         return out
 
     def checkpoint(self):

@@ -292,58 +292,3 @@ def test_every_cluster_size(cluster, precision):
         got = s.get_state()
     tol = 1e-12 if precision == gpspin.FP64 else 4e-6
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
-
-
-@pytest.mark.parametrize("precision", [gpspin.FP64, gpspin.FP32_MIXED])
-@pytest.mark.parametrize("mode", [IMAG, REAL])
-def test_split_passes_match_oracle(precision, mode):
-    """A pass split into a first launch of whole line groups and a second launch
-    with a finer tiling for the remaining lines (offset pointers, tables, trap
-    coordinates and partial norms) gives the oracle's result."""
-    p = ragged(nx=320, ny=288, xlen=0.05 * 320, ylen=0.05 * 288, dt=0.0005, precision=precision)
-    psi = smooth_plus_rough(p, 81)
-    want = oracle.propagate(p, psi, 20, mode)
-    with gpspin.Solver(p) as s:
-        s.set_state(psi)
-        s.set_tiling(0, cluster=1, lines_per_cta=2, mode=mode)
-        s.set_tiling(1, cluster=2, lines_per_cta=2, mode=mode)
-        s.set_split(0, 200, cluster=2, lines_per_cta=1, mode=mode)
-        s.set_split(1, 232, cluster=4, lines_per_cta=2, mode=mode)
-        t = s.tiling(mode)
-        assert t["xpass"]["split"]["first_lines"] == 200 and t["ypass"]["split"]["first_lines"] == 232
-        s.propagate(20, mode)  # 16 of them replayed from the captured graph
-        got = s.get_state()
-    tol = 1e-12 if precision == gpspin.FP64 else 2e-5
-    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
-
-
-def test_split_passes_real_time_fp64_bitwise():
-    """In real time a line's arithmetic does not depend on how lines are grouped
-    into launches: split and unsplit passes agree bitwise."""
-    p = ragged(nx=320, ny=288, xlen=0.05 * 320, ylen=0.05 * 288, dt=0.0005)
-    psi = smooth_plus_rough(p, 82)
-    out = []
-    for split in (False, True):
-        with gpspin.Solver(p) as s:
-            s.set_state(psi)
-            s.set_tiling(0, cluster=1, lines_per_cta=2, mode=REAL)
-            s.set_tiling(1, cluster=2, lines_per_cta=2, mode=REAL)
-            if split:
-                s.set_split(0, 200, cluster=2, lines_per_cta=1, mode=REAL)
-                s.set_split(1, 232, cluster=4, lines_per_cta=2, mode=REAL)
-            s.propagate(20, REAL)
-            out.append(s.get_state())
-    assert np.array_equal(out[0], out[1])
-
-
-def test_split_with_magnetization_constraint():
-    p = ragged(nx=320, ny=288, xlen=0.05 * 320, ylen=0.05 * 288, dt=0.0005, so_type=0, gamma=0.0, rabi=0.0)
-    psi = smooth_plus_rough(p, 83)
-    want = oracle.propagate_m(p, oracle.normalize_m(p, psi, 0.1), 10, 0.1)
-    with gpspin.Solver(p) as s:
-        s.set_state(oracle.normalize_m(p, psi, 0.1))
-        s.set_magnetization(0.1)
-        s.set_split(1, 200, cluster=2, lines_per_cta=1)
-        s.propagate(10, IMAG)
-        got = s.get_state()
-    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
