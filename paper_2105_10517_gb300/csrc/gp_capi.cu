@@ -116,7 +116,7 @@ static int solve_conflicts(int cs, int Lp, int nl3, int Qc, int G, int unit)
     return extra;
 }
 
-int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_req, LineTiling* t)
+int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_req, LineTiling* t, int compact)
 {
     if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
     if (S < 1 || S > 8 || (S & (S - 1)) || R < 1) return GP_ERR_ARG;  // portable cluster sizes
@@ -142,7 +142,7 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
     const int unit = single ? 2 : 1;
     const int G = single ? 8 : (c64 ? 16 : 8);
     int cs = m, Lp = Qc * m, best = -1;
-    for (int dc = 0; dc < G * unit; dc += unit)
+    for (int dc = 0; dc < (compact ? 1 : G * unit); dc += unit)
         for (int dl = 0; dl < G * unit; dl += unit) {
             const int c = m + dc, l = Qc * c + dl;
             const int k = solve_conflicts(c, l, 3 * R, Qc, G, unit);
@@ -1019,12 +1019,13 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
         LineTiling best = cur;
         float best_ms = -1.0f;
         const int ms_add[] = {0, 4, 8, 16, 32};
+        for (int compact : {0, 1})
         for (int S : {1, 2, 4, 8})
             for (int R : {1, 2, 4, 8})
                 for (int add : ms_add) {
                     LineTiling t;
-                    if (make_tiling(L, nl, cp, f32 ? TILE_C64_REG : TILE_C128, S, R, cur.m - (cur.m % 4) + add, &t) !=
-                        GP_OK)
+                    if (make_tiling(L, nl, cp, f32 ? TILE_C64_REG : TILE_C128, S, R, cur.m - (cur.m % 4) + add, &t,
+                                    compact) != GP_OK)
                         continue;
                     if (S > 1 && L < 64) continue;
                     float ms;

@@ -116,7 +116,10 @@ double max_cp(const gp_params& p, int dir, int mode);
 int choose_tiling(int L, int nlines, double cpmax, LineTiling* t, int kind = TILE_C128, int split = 1);
 // A specific tiling (autotuner candidates): S CTAs per line group, R lines per
 // CTA, chunk length m (raised to the minimum the precision needs).
-int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m, LineTiling* t);
+// compact = 1: chunk stride = chunk length (no chunk padding), the line-channel
+// stride padded for the fewest bank conflicts: less shared memory per CTA, which
+// can buy one more resident CTA per SM at the price of a few conflicts.
+int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m, LineTiling* t, int compact = 0);
 
 // launchers (gp_sweeps.cu)
 int launch_coef(LineCoef* coef, int nlines, int dir, int mode, double h, double line_len, double line_h,
