@@ -112,3 +112,32 @@ def test_plan_rejects_what_create_rejects():
     # |c'_inf| >= 1/2 (dt/h^2 far beyond the workloads): outside the tabulated solver
     with pytest.raises(gpspin.GPError):
         gpspin.plan_tiling(dict(p, dt=50.0))
+
+
+@pytest.mark.parametrize("mode", [gpspin.IMAG, gpspin.REAL])
+def test_supported_range_boundary(mode):
+    """The tabulated solver supports the systems whose Thomas recurrence contracts
+    by |c'_inf| < 1/2 (the chunk fixups then reach the rounding level within the
+    fixup table); beyond it gp_plan_tiling, like gp_create's first propagate,
+    refuses with GP_ERR_UNSUPPORTED.  The limit |c'_inf| is computed here
+    independently, by iterating the recurrence, on both sides of the boundary
+    in dt/h^2."""
+    base = dict(nx=64, ny=64, xlen=16.0, ylen=16.0, c0=50.0, c2=-2.0, omeg=0.3, so_type=1, gamma=0.4, rabi=0.1)
+    h2 = (16.0 / 64) ** 2
+    seen = set()
+    for r in np.geomspace(0.5, 40.0, 60):  # dt / h^2
+        p = dict(base, dt=r * h2)
+        cmax = 0.0
+        for d in (0, 1):
+            a, b, c = line_systems(p, d, mode)
+            cmax = max(cmax, float(np.max(np.abs(recurrence(a, b, c, 2000)[-1]))))
+        try:
+            gpspin.plan_tiling(p, mode)
+            ok = True
+        except gpspin.GPError as e:
+            assert e.status == 5  # GP_ERR_UNSUPPORTED
+            ok = False
+        if abs(cmax - 0.5) > 1e-3:  # away from the boundary itself, where rounding may decide
+            assert ok == (cmax < 0.5), (r, cmax, ok)
+        seen.add(ok)
+    assert seen == {True, False}  # the sweep crosses the boundary
