@@ -488,115 +488,6 @@ __device__ __forceinline__ void pointwise(C& a, C& b, C& c, C ev, typename RealO
     }
 }
 
-// ------------------------------------------- two complex64 sites at once --
-// The complex64 x-pass handles neighbouring sites in pairs.  Their pointwise
-// substeps and Sigma_y rotations run here in packed two-lane FP32 (lane .x the
-// first site, lane .y the second): every real operation of pointwise<MODE,
-// float2> and to_sigma_y becomes one two-lane instruction.  Each lane is rounded
-// exactly as the scalar instruction rounds it, and the operations and their
-// order are those of the scalar functions, so the results are bitwise those of
-// two scalar calls; only the instruction count halves.  Library expf / sincosf
-// and the large-argument series branch run per lane.
-struct C2 {
-    float2 re, im;  // one spinor component of the two sites
-};
-
-__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, p_neg(b)); }
-__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
-
-// v = M psi (spin_mv) for the two sites.
-__device__ __forceinline__ void spin_mv2(float2 bx, float2 by, float2 bz, const C2& a, const C2& b, const C2& c,
-                                         C2& va, C2& vb, C2& vc)
-{
-    va.re = p_fma(bz, a.re, p_fma(bx, b.re, p_mul(by, b.im)));
-    va.im = p_fma(bz, a.im, p_fma(bx, b.im, p_mul(p_neg(by), b.re)));
-    vb.re = p_fma(bx, a.re, p_fma(p_neg(by), a.im, p_fma(bx, c.re, p_mul(by, c.im))));
-    vb.im = p_fma(bx, a.im, p_fma(by, a.re, p_fma(bx, c.im, p_mul(p_neg(by), c.re))));
-    vc.re = p_fma(bx, b.re, p_fma(p_neg(by), b.im, p_mul(p_neg(bz), c.re)));
-    vc.im = p_fma(bx, b.im, p_fma(by, b.re, p_mul(p_neg(bz), c.im)));
-}
-
-// pointwise<MODE, float2> with ev = 1 for the two sites (tv = dt V per lane).
-template <int MODE>
-__device__ __forceinline__ void pointwise2(C2& a, C2& b, C2& c, float2 tv, const PConstT<float>& k, float2& ps)
-{
-    const float2 rp = p_fma(a.re, a.re, p_mul(a.im, a.im));
-    const float2 r0 = p_fma(b.re, b.re, p_mul(b.im, b.im));
-    const float2 rm = p_fma(c.re, c.re, p_mul(c.im, c.im));
-    const float2 rho = p_add(p_add(rp, r0), rm);
-    const float2 fr = p_fma(a.re, b.re, p_fma(a.im, b.im, p_fma(b.re, c.re, p_mul(b.im, c.im))));
-    const float2 fi = p_fma(a.re, b.im, p_fma(p_neg(a.im), b.re, p_fma(b.re, c.im, p_mul(p_neg(b.im), c.re))));
-    const float2 bx = p_fma(splat(k.dtc2), fr, splat(k.dtr));
-    const float2 by = p_mul(splat(k.dtc2), fi);
-    const float2 bz = p_mul(splat(k.dtc2), p_sub(rp, rm));
-    const float2 u = p_fma(splat(2.0f), p_fma(bx, bx, p_mul(by, by)), p_mul(bz, bz));
-    float2 s1, s2;
-    if (u.x <= 0.01f && u.y <= 0.01f) {
-        const float2 su = MODE == 1 ? p_neg(u) : u;
-        s1 = p_fma(p_fma(su, splat(1.0f / 120.0f), splat(1.0f / 6.0f)), su, splat(1.0f));
-        s2 = p_fma(p_fma(su, splat(1.0f / 720.0f), splat(1.0f / 24.0f)), su, splat(0.5f));
-    } else {
-        spin_series<MODE>(u.x, s1.x, s2.x);
-        spin_series<MODE>(u.y, s1.y, s2.y);
-    }
-    C2 va, vb, vc, wa, wb, wc;
-    spin_mv2(bx, by, bz, a, b, c, va, vb, vc);
-    spin_mv2(bx, by, bz, va, vb, vc, wa, wb, wc);
-    const float2 x = p_fma(splat(k.dtc0), rho, tv);
-    if (MODE == 1) {
-        // t = psi - i s1 v - s2 w
-        const float2 ms1 = p_neg(s1), ms2 = p_neg(s2);
-        C2 ta, tb, tc;
-        ta.re = p_fma(s1, va.im, p_fma(ms2, wa.re, a.re));
-        ta.im = p_fma(ms1, va.re, p_fma(ms2, wa.im, a.im));
-        tb.re = p_fma(s1, vb.im, p_fma(ms2, wb.re, b.re));
-        tb.im = p_fma(ms1, vb.re, p_fma(ms2, wb.im, b.im));
-        tc.re = p_fma(s1, vc.im, p_fma(ms2, wc.re, c.re));
-        tc.im = p_fma(ms1, vc.re, p_fma(ms2, wc.im, c.im));
-        float2 cs, sn;
-        scalar_cis(x.x, cs.x, sn.x);
-        scalar_cis(x.y, cs.y, sn.y);
-        // ph = s exp(-i x)
-        const float2 phr = p_mul(splat(k.s), cs), phi = p_mul(splat(k.s), p_neg(sn));
-        auto cm = [&](const C2& t) {
-            C2 r;
-            r.re = p_fma(phr, t.re, p_mul(p_neg(phi), t.im));
-            r.im = p_fma(phr, t.im, p_mul(phi, t.re));
-            return r;
-        };
-        a = cm(ta);
-        b = cm(tb);
-        c = cm(tc);
-        ps = splat(1.0f);
-    } else {
-        ps = p_mul(splat(k.s), make_float2(scalar_exp(x.x), scalar_exp(x.y)));
-        const float2 ms1 = p_neg(s1);
-        a.re = p_fma(ms1, va.re, p_fma(s2, wa.re, a.re));
-        a.im = p_fma(ms1, va.im, p_fma(s2, wa.im, a.im));
-        b.re = p_fma(ms1, vb.re, p_fma(s2, wb.re, b.re));
-        b.im = p_fma(ms1, vb.im, p_fma(s2, wb.im, b.im));
-        c.re = p_fma(ms1, vc.re, p_fma(s2, wc.re, c.re));
-        c.im = p_fma(ms1, vc.im, p_fma(s2, wc.im, c.im));
-    }
-}
-
-// to_sigma_y for the two sites.
-__device__ __forceinline__ void to_sigma_y2(const C2& a, const C2& b, const C2& c, float2 ps, C2& p, C2& z, C2& m)
-{
-    const float2 rs2 = p_mul(splat(0.70710678118654752440f), ps), half = p_mul(splat(0.5f), ps);
-    const float2 dx = p_mul(half, p_sub(a.re, c.re)), dy = p_mul(half, p_sub(a.im, c.im));
-    p.re = p_fma(rs2, b.im, dx);
-    p.im = p_fma(p_neg(rs2), b.re, dy);
-    m.re = p_fma(p_neg(rs2), b.im, dx);
-    m.im = p_fma(rs2, b.re, dy);
-    z.re = p_mul(rs2, p_add(a.re, c.re));
-    z.im = p_mul(rs2, p_add(a.im, c.im));
-}
-
 // --------------------------------------------------------- basis rotations --
 // phi = U_y^dagger (ps psi): Sigma_y eigen-channels lambda = +1, 0, -1 with
 // eigenvectors (1, i sqrt2, -1)/2, (1, 0, 1)/sqrt2, (1, -i sqrt2, -1)/2, and a
@@ -1108,23 +999,12 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
                 const int r = div_lh(q), kl = 2 * (q - r * Lh), i = k0 + kl, j = line0 + r;
                 float4* row = reinterpret_cast<float4*>(sa + r * 3 * Lp + kl + (kl / M) * pad);
                 const float4 va = row[0], vb = row[q4], vc = row[2 * q4];
-                // the two sites in packed two-lane form
-                C2 a{make_float2(va.x, va.z), make_float2(va.y, va.w)};
-                C2 b{make_float2(vb.x, vb.z), make_float2(vb.y, vb.w)};
-                C2 c{make_float2(vc.x, vc.z), make_float2(vc.y, vc.w)};
-                float2 ps = splat(k.s);  // channels pass through, with the pending normalisation
-                if (A.do_p) {
-                    // dt V joins the scalar exponent (no table loads)
-                    const R yy = fma(R(j), tk.fdy, tk.fy0);
-                    const float2 xx = p_fma(make_float2(R(i), R(i + 1)), splat(tk.fdx), splat(tk.fx0));
-                    const float2 tv = p_fma(p_mul(splat(tk.hx), xx), xx, splat(tk.hy * yy * yy));
-                    pointwise2<MODE>(a, b, c, tv, k, ps);
-                }
-                C2 p, z, m;
-                to_sigma_y2(a, b, c, ps, p, z, m);
-                row[0] = make_float4(p.re.x, p.im.x, p.re.y, p.im.y);
-                row[q4] = make_float4(z.re.x, z.im.x, z.re.y, z.im.y);
-                row[2 * q4] = make_float4(m.re.x, m.im.x, m.re.y, m.im.y);
+                C p0, z0, m0, p1, z1, m1;
+                site(mkc<C>(va.x, va.y), mkc<C>(vb.x, vb.y), mkc<C>(vc.x, vc.y), i, j, p0, z0, m0);
+                site(mkc<C>(va.z, va.w), mkc<C>(vb.z, vb.w), mkc<C>(vc.z, vc.w), i + 1, j, p1, z1, m1);
+                row[0] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                row[q4] = make_float4(z0.x, z0.y, z1.x, z1.y);
+                row[2 * q4] = make_float4(m0.x, m0.y, m1.x, m1.y);
             }
         }
     }
