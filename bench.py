@@ -73,10 +73,10 @@ BYTES_PER_SITE_PASS = 96
 # one ncu capture of that kernel), keyed by kernel and workload and valid only
 # while the kernel source is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
-    "xpass_kernel<0, double2> vortex512": (16210432 + 512, "eb250b4a7edbda2f"),
-    "ypass_kernel<0, double2> vortex512": (16175104 + 256, "eb250b4a7edbda2f"),
-    "xpass_kernel_reg<0, float2, 32> precision2048": (105435136 + 56283136, "eb250b4a7edbda2f"),
-    "ypass_kernel_reg<0, float2, 32> precision2048": (105467648 + 57590528, "eb250b4a7edbda2f"),
+    "xpass_kernel<1, double2> quench1024": (59583232 + 5544448, "0ae55a197a1a1d58"),
+    "ypass_kernel<1, double2> quench1024": (59104256 + 6420736, "0ae55a197a1a1d58"),
+    "xpass_kernel_reg<0, float2, 32> precision2048": (105457408 + 55663360, "0ae55a197a1a1d58"),
+    "ypass_kernel_reg<0, float2, 32> precision2048": (105458432 + 57474560, "0ae55a197a1a1d58"),
 }
 
 L2_FLUSH_BYTES = 256 << 20
