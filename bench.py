@@ -110,6 +110,8 @@ def parse():
     ap.add_argument("--cap", type=int, default=20000)
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-plain", action="store_true", help="serving: skip the one-at-a-time FP64 baseline")
+    ap.add_argument("--max-running-sites", type=int, default=1 << 21,
+                    help="serving: grid points of the solves running at once (0: admit by memory only)")
     ap.add_argument("--no-autotune", action="store_true", help="time the default tiling instead of the tuned one")
     ap.add_argument("--tiling", default=None,
                     help="S,R,m: cluster size, lines per CTA and chunk length of both passes (instead of autotuning)")
@@ -601,9 +603,11 @@ def run_serving(args):
     budget = int(free * 0.8)
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
+    lim = args.max_running_sites
     mixed, rm = serve.serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=budget, cap=args.cap,
-                                    tol=args.tol)
-    b64, rb = serve.serve_batched(trace, policy=gpspin.POLICY_FP64, max_bytes=budget, cap=args.cap, tol=args.tol)
+                                    tol=args.tol, max_running_sites=lim)
+    b64, rb = serve.serve_batched(trace, policy=gpspin.POLICY_FP64, max_bytes=budget, cap=args.cap, tol=args.tol,
+                                  max_running_sites=lim)
     if args.no_plain:  # batched FP64 equals the plain path to rounding (tested): use it as the reference
         plain, rp = dict(b64, note="not run; batched FP64 used as the reference"), rb
     else:
@@ -655,7 +659,7 @@ def run_serving(args):
         "speedup_solves_per_s_vs_plain": mixed["solves_per_s"] / plain["solves_per_s"],
         "speedup_fp64_batched_vs_plain": b64["solves_per_s"] / plain["solves_per_s"],
         "energy_agreement_vs_plain_fp64": {"batched_mixed": agreement(rm), "batched_fp64": agreement(rb)},
-        "device_budget_bytes": budget, "clocks": clocks.summary(),
+        "device_budget_bytes": budget, "max_running_sites": lim, "clocks": clocks.summary(),
     }
 
 

@@ -257,6 +257,12 @@ int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req,
  * solves is unchanged (the default, enable != 0); enable = 0 launches every
  * kernel of every tick directly.  Results are bitwise the same either way. */
 int gp_batch_use_graphs(gp_batch* b, int enable);
+/* Limits the work in flight: a queued request is admitted only while the grid
+ * points (nx * ny) of all running solves plus its own stay within max_sites,
+ * except that one solve always runs; 0: no limit (admission by memory only).
+ * With a limit that still fills the GPU, earlier requests take a larger share
+ * of it and finish sooner, at the same solves/s. */
+int gp_batch_set_running_limit(gp_batch* b, long long max_sites);
 /* Limits the number of queued (not yet admitted) requests; 0: no limit. */
 int gp_batch_set_queue_limit(gp_batch* b, int max_queued);
 /* Cancels a queued or running solve between ticks: a queued one leaves the

@@ -169,6 +169,7 @@ struct gp_batch {
     int* counts = nullptr;  // device: kGroupCounts per precision group (complex128, complex64)
     int* flag = nullptr;
     int max_queued = 0;     // 0: no limit on queued requests
+    long long max_sites = 0;  // 0: no limit on the grid points of the running solves
     bool graphs = true;     // replay captured ticks while the running set is unchanged
     cudaStream_t stream32 = nullptr;  // the complex64 group runs beside the complex128 one
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -306,6 +307,14 @@ int running_count(const gp_batch* b)
     return n;
 }
 
+long long running_sites(const gp_batch* b)
+{
+    long long n = 0;
+    for (const auto& kv : b->reqs)
+        if (kv.second.state == GP_REQ_RUNNING) n += (long long)kv.second.p.nx * kv.second.p.ny;
+    return n;
+}
+
 // Admits queued requests in arrival order while their footprint fits.
 int admit(gp_batch* b)
 {
@@ -318,6 +327,11 @@ int admit(gp_batch* b)
             continue;
         }
         if (b->used_bytes + q.bytes > b->max_bytes) break;
+        // enough work in flight to fill the GPU: later requests wait, so earlier
+        // ones get more of the GPU and finish sooner (arrival order is kept)
+        if (b->max_sites > 0 && running_count(b) > 0 &&
+            running_sites(b) + (long long)q.p.nx * q.p.ny > b->max_sites)
+            break;
         gp_handle* h = nullptr;
         int st = gp_create(&q.p, b->stream, &h);
         // The device is fuller than the accounting: wait for retirements while
@@ -514,6 +528,13 @@ int gp_batch_use_graphs(gp_batch* b, int enable)
         b->g64.drop_graph();
         b->g32.drop_graph();
     }
+    return GP_OK;
+}
+
+int gp_batch_set_running_limit(gp_batch* b, long long max_sites)
+{
+    if (!b || max_sites < 0) return GP_ERR_ARG;
+    b->max_sites = max_sites;
     return GP_OK;
 }
 

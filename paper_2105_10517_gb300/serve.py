@@ -34,7 +34,7 @@ def _summary(records, makespan):
 
 
 def serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=64 << 30, check_every=100, tol=1e-9,
-                  tol32=1e-7, cap=20000, refine_steps=2000, stream=None, deadline_s=None):
+                  tol32=1e-7, cap=20000, refine_steps=2000, stream=None, deadline_s=None, max_running_sites=0):
     """Continuous batching over the trace; returns (summary, per-request records).
     With deadline_s, a request still queued or running that long after its
     arrival is cancelled (its memory is released for the others) and recorded
@@ -42,6 +42,7 @@ def serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=64 << 30, c
     pending = sorted(trace, key=lambda r: r["arrival"])
     records, live = [], {}
     with gpspin.Batch(max_bytes, check_every=check_every, stream=stream) as b:
+        b.set_running_limit(max_running_sites)
         t0 = time.perf_counter()
         k = 0
         while k < len(pending) or live:

@@ -121,3 +121,25 @@ def test_graph_ticks_equal_direct_ticks_bitwise():
     for x, y in zip(a, b):
         assert x[0] == y[0] == gpspin.REQ_DONE and x[1] == y[1]
         assert np.array_equal(x[3], y[3])
+
+
+def test_running_limit_admits_by_work_in_flight():
+    """With a limit on the grid points of the running solves, requests wait for
+    work to finish (arrival order kept, one solve always runs), and their
+    results are bitwise those of the unlimited batch."""
+    items = [(req_params(64), dict(seed=s, tol=1e-300, cap=40)) for s in range(3)]
+    free = run_batch(items)
+    out = {}
+    with gpspin.Batch(8 << 30, check_every=CHECK) as b:
+        b.set_running_limit(64 * 64 + 100)  # room for one 64^2 solve at a time
+        ids = [b.submit(p, **kw) for p, kw in items]
+        nr, nq = b.step()
+        assert (nr, nq) == (1, 2)
+        for _ in range(20):
+            nr, nq = b.step()
+            if nr == 0 and nq == 0:
+                break
+        for i in ids:
+            out[i] = b.poll(i, fetch=True, release=True)
+    for f, i in zip(free, ids):
+        assert out[i][0] == gpspin.REQ_DONE and np.array_equal(out[i][3], f[3])
