@@ -54,15 +54,16 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 #   y-pass: Thomas 3 x 22 + U_x 16 + |psi|^2 partial sums 12
 FLOPS_PER_SITE = {"xpass": 252, "ypass": 94}
 INST_PER_SITE = {"xpass": 155, "ypass": 57}
-# Real time, same counting: the Thomas pivots are complex (26 flops, 14
-# instructions per channel point: forward cmul + cfnma, back cfnma, 2w - phi), and
-# P applies exp(-i dt (V + c0 rho)) as a complex phase (cis series, trap factor
-# product, three complex products) and has no partial norms.
-#   x-pass: P 192 (77 FMA, 35 MUL, 3 ADD; 115 instructions) + U_y^dag 16 (12)
+# Real time, same counting (dt c0 rho <= 1/64): the Thomas pivots are complex (26
+# flops, 14 instructions per channel point: forward cmul + cfnma, back cfnma,
+# 2w - phi), and P applies exp(-i dt (V + c0 rho)) as a complex phase (cis
+# series of four terms each, trap factor product, three complex products) and
+# has no partial norms.
+#   x-pass: P 182 (73 FMA, 33 MUL, 3 ADD; 109 instructions) + U_y^dag 16 (12)
 #           + Thomas 3 x 26 (3 x 14) + U_x^dag U_y 14 (14)
 #   y-pass: Thomas 3 x 26 (3 x 14) + U_x 16 (12)
-FLOPS_PER_SITE_REAL = {"xpass": 300, "ypass": 94}
-INST_PER_SITE_REAL = {"xpass": 183, "ypass": 54}
+FLOPS_PER_SITE_REAL = {"xpass": 290, "ypass": 94}
+INST_PER_SITE_REAL = {"xpass": 177, "ypass": 54}
 # Closing x-pass of a second-order (Strang) step, same counting: U_y^dag with the
 # scale 18 + Thomas 3 x 22 + U_y 14 + P 160 (applied after the solve, with its
 # scale) + |psi|^2 partial sums 12.

@@ -329,9 +329,10 @@ __global__ void trap_table_kernel(C* out, int n, double len, double w, double dt
 //   real:      exp(-iM) = I - i s1(u) M - s2(u) M^2, s1 = sin(t)/t,  s2 = (1 - cos t)/t^2
 // with t = sqrt(u); both are power series in u, used directly: three terms for
 // u <= 1e-4 and five for u <= 1/100 (first omitted term <= 2.5e-18 relative).
-// The scalar factor exp(-tau' c0 rho) is a Taylor series: eight terms for
-// dt c0 rho <= 1/64 (imaginary time) and eleven/twelve terms up to 1/8 (<= 3e-18);
-// larger arguments take the library exp / sincos.  The trap factor comes from
+// The scalar factor exp(-tau' c0 rho) is a Taylor series: eight terms (imaginary
+// time) or four plus four (cos, sin in real time) for dt c0 rho <= 1/64, and
+// eleven/twelve terms up to 1/8 (<= 3e-18); larger arguments take the library
+// exp / sincos.  The trap factor comes from
 // the per-axis tables.  The complex64 version evaluates the same formulas in
 // FP32 (three-term series for u <= 1/100, library expf / sincosf otherwise).
 template <typename R>
@@ -428,7 +429,12 @@ __device__ __forceinline__ float scalar_exp(float x) { return expf(-x); }
 
 __device__ __forceinline__ void scalar_cis(double x, double& cs, double& sn)
 {
-    if (x <= 0.125) {
+    if (x <= 0.015625) {
+        // x <= 1/64: the first omitted terms x^8/8! and x^9/9! are <= 1e-19
+        double x2 = x * x;
+        cs = fma(fma(fma(x2, -1.0 / 720.0, 1.0 / 24.0), x2, -0.5), x2, 1.0);
+        sn = x * fma(fma(fma(x2, -1.0 / 5040.0, 1.0 / 120.0), x2, -1.0 / 6.0), x2, 1.0);
+    } else if (x <= 0.125) {
         double x2 = x * x;
         cs = fma(fma(fma(fma(fma(x2, -1.0 / 3628800.0, 1.0 / 40320.0), x2, -1.0 / 720.0), x2, 1.0 / 24.0), x2, -0.5),
                  x2, 1.0);
@@ -474,8 +480,9 @@ __device__ __forceinline__ void pointwise(C& a, C& b, C& c, C ev, typename RealO
         C tc = mkc<C>(fma(s1, vc.y, fma(-s2, wc.x, c.x)), fma(-s1, vc.x, fma(-s2, wc.y, c.y)));
         R cs, sn;
         scalar_cis(x, cs, sn);
-        // ph = s ev exp(-i x)
-        C ph = mkc<C>(k.s * fma(ev.x, cs, ev.y * sn), k.s * fma(ev.y, cs, -ev.x * sn));
+        // ph = ev exp(-i x): nothing is pending in real time (every real-time
+        // step starts from an applied normalisation, s = 1 exactly)
+        C ph = mkc<C>(fma(ev.x, cs, ev.y * sn), fma(ev.y, cs, -ev.x * sn));
         a = cmul(ph, ta);
         b = cmul(ph, tb);
         c = cmul(ph, tc);
