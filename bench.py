@@ -111,7 +111,7 @@ def parse():
     ap.add_argument("--cap", type=int, default=20000)
     ap.add_argument("--tol", type=float, default=1e-9)
     ap.add_argument("--no-plain", action="store_true", help="serving: skip the one-at-a-time FP64 baseline")
-    ap.add_argument("--max-running-sites", type=int, default=1 << 21,
+    ap.add_argument("--max-running-sites", type=int, default=1 << 22,
                     help="serving: grid points of the solves running at once (0: admit by memory only)")
     ap.add_argument("--no-autotune", action="store_true", help="time the default tiling instead of the tuned one")
     ap.add_argument("--tiling", default=None,
