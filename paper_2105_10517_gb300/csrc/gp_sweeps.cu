@@ -190,10 +190,11 @@ __device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, 
     return mbar_wait_bounded(mbar, err);
 }
 
-// One-array layout: stages the chunks of the CTA's line segments, one bulk copy
-// per chunk issued by the thread that solves it (u = ql * 3 nl + lc), chunk
-// (lc, ql) of line point k0 + ql m .. to dst[lc * Lp + ql * cs].  Rows must be
-// 16-byte aligned (even L); m, cs and Lp are even.
+// Stages the chunks of the CTA's line segments into their slots of the line
+// array, one bulk copy per chunk issued by the thread that solves it
+// (u = ql * 3 nl + lc): chunk (lc, ql) of line point k0 + ql m .. to
+// dst[lc * Lp + ql * cs].  Every copy must start on a 16-byte boundary and move a
+// multiple of 16 bytes: complex128 always; complex64 with even L, m, cs and Lp.
 template <typename C>
 __device__ __forceinline__ bool stage_chunks(C* dst, const C* base, size_t plane, int line0, int nl, int L, int k0,
                                              int len, int m, int cs, int Lp, uint64_t* mbar, int* err)
@@ -1208,10 +1209,14 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
             cluster_arrive_relaxed();
         }
     }
-    // with one line array (M > 0) the chunks are staged in place and need no copy
+    // The chunks are staged straight into their slots of the line array, one
+    // bulk copy per chunk, and need no copy: with one line array (M > 0), and for
+    // complex128, whose 16-byte elements keep every chunk copy 16-byte aligned.
+    // Complex64 with the shared-memory solve stages whole rows and copies them in.
+    constexpr bool in_place = M > 0 || sizeof(C) == 16;
     bool ok = true;
     if (T.bulk && Ll > 0) {
-        if constexpr (M > 0)
+        if constexpr (in_place)
             ok = stage_chunks(sa, A.in, plane, line0, nl, L, k0, Ll, T.m, T.cs, T.Lp, &mbar, A.err);
         else
             ok = stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, Ll, &mbar, A.err);
@@ -1220,7 +1225,7 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     const FastDiv div_len(Ll), div_nl(nl);
     const SPos spos(T);
     const int Lp = T.Lp;
-    const bool copy_in = !(M > 0 && T.bulk);
+    const bool copy_in = !(in_place && T.bulk);
     for (int e = threadIdx.x; copy_in && threadIdx.x < T.threads && e < nl * Ll; e += T.threads) {
         int r = div_len(e), kl = e - r * Ll, j = k0 + kl, i = line0 + r;
         C* dst = sa + r * 3 * Lp + spos(kl);
