@@ -74,10 +74,10 @@ BYTES_PER_SITE_PASS = 96
 # one ncu capture of that kernel), keyed by kernel and workload and valid only
 # while the kernel source is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
-    "xpass_kernel<1, double2> quench1024": (59583232 + 5544448, "0ae55a197a1a1d58"),
-    "ypass_kernel<1, double2> quench1024": (59104256 + 6420736, "0ae55a197a1a1d58"),
-    "xpass_kernel_reg<0, float2, 32> precision2048": (105457408 + 55663360, "0ae55a197a1a1d58"),
-    "ypass_kernel_reg<0, float2, 32> precision2048": (105458432 + 57474560, "0ae55a197a1a1d58"),
+    "xpass_kernel<1, double2> quench1024": (59190528 + 5368576, "cfb31e554006dbf4"),
+    "ypass_kernel<1, double2> quench1024": (58736384 + 6190848, "cfb31e554006dbf4"),
+    "xpass_kernel_reg<0, float2, 32> precision2048": (105458432 + 55552000, "cfb31e554006dbf4"),
+    "ypass_kernel_reg<0, float2, 32> precision2048": (105446144 + 56904704, "cfb31e554006dbf4"),
 }
 
 L2_FLUSH_BYTES = 256 << 20
