@@ -568,8 +568,9 @@ def run_reference(args):
     oracle.build()
     cores = oracle.set_threads(host_cores())
     c, p = workload(args.workload)
-    # calibrate: size the sample grid so that warmup + steps take about two minutes
-    r, _, _ = oracle_rate(p, 64, 3, mode=c["mode"])
+    # calibrate: size the sample grid so that warmup + steps take about two
+    # minutes (on a grid large enough for the threads to have work)
+    r, _, _ = oracle_rate(p, min(256, p["nx"]), 3, mode=c["mode"])
     budget = 120.0 / max(1, args.steps + args.warmup)
     n = int(max(16, min(p["nx"], math.sqrt(budget * r))))
     oracle_rate(p, n, max(1, args.warmup), mode=c["mode"])
