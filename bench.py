@@ -76,6 +76,8 @@ BYTES_PER_SITE_PASS = 96
 NCU_TRAFFIC = {
     "xpass_kernel<1, double2> quench1024": (59190528 + 5368576, "cfb31e554006dbf4"),
     "ypass_kernel<1, double2> quench1024": (58736384 + 6190848, "cfb31e554006dbf4"),
+    "xpass_kernel<0, double2> vortex512": (16203008 + 768, "cfb31e554006dbf4"),
+    "ypass_kernel<0, double2> vortex512": (16174336 + 256, "cfb31e554006dbf4"),
     "xpass_kernel_reg<0, float2, 32> precision2048": (105458432 + 55552000, "cfb31e554006dbf4"),
     "ypass_kernel_reg<0, float2, 32> precision2048": (105446144 + 56904704, "cfb31e554006dbf4"),
 }
