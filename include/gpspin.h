@@ -257,6 +257,13 @@ int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req,
  * solves is unchanged (the default, enable != 0); enable = 0 launches every
  * kernel of every tick directly.  Results are bitwise the same either way. */
 int gp_batch_use_graphs(gp_batch* b, int enable);
+/* Launch form of the batched passes; each substep (and solve kind) is one
+ * launch over the (instance, line group) work items of every running solve,
+ * largest grids first.  max_ctas < 0 (the default): one CTA per work item;
+ * max_ctas = 0: persistent, one CTA per resident slot, the CTAs taking the work
+ * items from a device counter; max_ctas > 0: persistent with at most max_ctas
+ * CTAs.  Results are bitwise the same in every form. */
+int gp_batch_set_persistent(gp_batch* b, int max_ctas);
 /* Limits the work in flight: a queued request is admitted only while the grid
  * points (nx * ny) of all running solves plus its own stay within max_sites,
  * except that one solve always runs; 0: no limit (admission by memory only).

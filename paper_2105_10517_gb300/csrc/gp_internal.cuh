@@ -136,15 +136,22 @@ int launch_xpass(const PassArgsF& a, int mode, cudaStream_t st);
 int launch_ypass(const PassArgsF& a, int mode, cudaStream_t st);
 // Batched passes over (instance, CTA) work items; m_reg = 16/24/32 selects the
 // register-resident solve (every item's tiling one-array with that m), 0 the
-// shared-memory solve.
+// shared-memory solve.  work: null for one CTA per item; else two device ints,
+// zero before the launch and zero again after it, that make the launch
+// persistent (one CTA per resident slot, items taken from a counter), with at
+// most max_ctas CTAs if max_ctas > 0.
 int launch_xpass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st, int m_reg = 0);
+                         size_t smem, int mode, cudaStream_t st, int m_reg = 0, int* work = nullptr,
+                         int max_ctas = 0);
 int launch_ypass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st, int m_reg = 0);
+                         size_t smem, int mode, cudaStream_t st, int m_reg = 0, int* work = nullptr,
+                         int max_ctas = 0);
 int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st, int m_reg = 0);
+                         size_t smem, int mode, cudaStream_t st, int m_reg = 0, int* work = nullptr,
+                         int max_ctas = 0);
 int launch_ypass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st, int m_reg = 0);
+                         size_t smem, int mode, cudaStream_t st, int m_reg = 0, int* work = nullptr,
+                         int max_ctas = 0);
 // the bounded mbarrier wait of the passes on a barrier nothing arrives on
 int launch_wait_probe(int tries, int* err, cudaStream_t st);
 // launchers (gp_reduce.cu)

@@ -12,6 +12,8 @@
 #include "gp_internal.cuh"
 #include <cmath>
 #include <cooperative_groups.h>
+#include <mutex>
+#include <vector>
 
 namespace cg = cooperative_groups;
 
@@ -90,19 +92,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* m, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait on phase 0 of the barrier.  Returns true (for the whole CTA) once
-// the copies have landed; if any thread gives up after `tries` polls, the
-// CTA sets bit 8 of *err, waits once more (again bounded) so that no copy is
-// still writing its shared memory, and returns false.
+// Bounded wait on the phase of the barrier with the given parity (phase 0 for a
+// barrier used once).  Returns true (for the whole CTA) once the copies have
+// landed; if any thread gives up after `tries` polls, the CTA sets bit 8 of
+// *err, waits once more (again bounded) so that no copy is still writing its
+// shared memory, and returns false.
 constexpr int kWaitTries = 1 << 22;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err, int tries = kWaitTries)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* m, int* err, int tries = kWaitTries, uint32_t parity = 0)
 {
     bool ok = false;
-    for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, 0);
+    for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, parity);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0 && err) atomicOr(err, 8);
-        for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, 0);
+        for (int it = 0; it < tries && !ok; ++it) ok = mbar_try_wait(m, parity);
         __syncthreads();
         return false;
     }
@@ -173,11 +176,13 @@ __device__ __forceinline__ void wait_carry(uint64_t* bar, int* err)
 // Stages row segments base + c * plane + (line0 + r) * L + k0 .. + len for
 // r < nl, c < 3 into dst[(r * 3 + c) * stride].  Segments and destination rows
 // must be 16-byte aligned and a multiple of 16 bytes long.
+// phase < 0: the barrier is initialised here and used once; phase >= 0: it was
+// initialised by the caller and has completed `phase` earlier stagings.
 template <typename C>
 __device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, int line0, int nl, int L, int k0,
-                                           int len, int stride, uint64_t* mbar, int* err)
+                                           int len, int stride, uint64_t* mbar, int* err, int phase = -1)
 {
-    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    if (threadIdx.x == 0 && phase < 0) mbar_init(mbar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t seg_bytes = (uint32_t)(len * sizeof(C));
@@ -187,7 +192,7 @@ __device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, 
                 bulk_g2s(dst + (size_t)(r * 3 + c) * stride, base + c * plane + (size_t)(line0 + r) * L + k0, seg_bytes,
                          mbar);
     }
-    return mbar_wait_bounded(mbar, err);
+    return mbar_wait_bounded(mbar, err, kWaitTries, phase < 0 ? 0u : (uint32_t)(phase & 1));
 }
 
 // Stages the chunks of the CTA's line segments into their slots of the line
@@ -195,12 +200,13 @@ __device__ __forceinline__ bool stage_rows(C* dst, const C* base, size_t plane, 
 // (u = ql * 3 nl + lc): chunk (lc, ql) of line point k0 + ql m .. to
 // dst[lc * Lp + ql * cs].  Every copy must start on a 16-byte boundary and move a
 // multiple of 16 bytes: complex128 always; complex64 with even L, m, cs and Lp.
+// `phase` as for stage_rows.
 template <typename C>
 __device__ __forceinline__ bool stage_chunks(C* dst, const C* base, size_t plane, int line0, int nl, int L, int k0,
-                                             int len, int m, int cs, int Lp, uint64_t* mbar, int* err)
+                                             int len, int m, int cs, int Lp, uint64_t* mbar, int* err, int phase = -1)
 {
     if (threadIdx.x == 0) {
-        mbar_init(mbar, 1);
+        if (phase < 0) mbar_init(mbar, 1);
         mbar_expect_tx(mbar, (uint32_t)(3 * nl * len * sizeof(C)));
     }
     __syncthreads();
@@ -211,7 +217,7 @@ __device__ __forceinline__ bool stage_chunks(C* dst, const C* base, size_t plane
         bulk_g2s(dst + lc * Lp + ql * cs, base + c * plane + (size_t)(line0 + r) * L + k0 + k,
                  (uint32_t)(n * sizeof(C)), mbar);
     }
-    return mbar_wait_bounded(mbar, err);
+    return mbar_wait_bounded(mbar, err, kWaitTries, phase < 0 ? 0u : (uint32_t)(phase & 1));
 }
 
 // The part of a line group one CTA works on: lines line0 .. line0 + nl - 1,
@@ -894,9 +900,12 @@ struct SPos {
 // TAIL (second-order splitting, complex128): the solve comes first and the pass
 // ends with psi = U_y phi', the pointwise substep, a natural-layout store and the
 // per-CTA partial norms (wsum: warp sums).
+// phase: null for a CTA that runs one item (the staging barrier is initialised
+// here); in a persistent CTA the count of stagings its barrier has completed,
+// advanced here, or negative after a staging wait gave up.
 template <int MODE, typename C, int M, bool TAIL = false>
 __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar,
-                                           uint64_t* cbar, double* wsum = nullptr)
+                                           uint64_t* cbar, double* wsum = nullptr, int* phase = nullptr)
 {
     typedef typename RealOf<C>::type R;
     const LineTiling& T = A.t;
@@ -928,10 +937,12 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     // with one line array (M > 0) the chunks are staged in place
     bool ok = true;
     if (T.bulk && Ll > 0) {
+        const int ph = phase ? *phase : -1;
         if constexpr (M > 0)
-            ok = stage_chunks(sa, A.in, plane, line0, nl, L, k0, Ll, T.m, T.cs, T.Lp, &mbar, A.err);
+            ok = stage_chunks(sa, A.in, plane, line0, nl, L, k0, Ll, T.m, T.cs, T.Lp, &mbar, A.err, ph);
         else
-            ok = stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, Ll, &mbar, A.err);
+            ok = stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, Ll, &mbar, A.err, ph);
+        if (phase) *phase = ok ? ph + 1 : -1;
     }
 
     // Pointwise constants.  The complex64 pass takes them rounded to FP32 on the
@@ -1150,41 +1161,13 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) xpass_kernel_reg(
     xpass_body<MODE, C, M>(A, blockIdx.x, smem_raw, mbar, cbar);
 }
 
-// Many instances in one launch: CTA b works on item items[b] = (instance, cta)
-// for b < *n_items (the launch may be larger than the current item count).
-template <int MODE, typename C>
-__global__ void __launch_bounds__(512) xpass_batched(const PassArgsT<C>* args, const int2* items, const int* n_items)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t mbar;
-    __shared__ uint64_t cbar[2];
-    if ((int)blockIdx.x >= *n_items) return;
-    const int2 it = items[blockIdx.x];
-    const PassArgsT<C> A = args[it.x];
-    xpass_body<MODE, C, 0>(A, it.y, smem_raw, mbar, cbar);
-}
-
-// The same with the register-resident solve: every item's tiling is a one-array
-// tiling of chunk length M.
-template <int MODE, typename C, int M>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
-    xpass_batched_reg(const PassArgsT<C>* args, const int2* items, const int* n_items)
-{
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t mbar;
-    __shared__ uint64_t cbar[2];
-    if ((int)blockIdx.x >= *n_items) return;
-    const int2 it = items[blockIdx.x];
-    const PassArgsT<C> A = args[it.x];
-    xpass_body<MODE, C, M>(A, it.y, smem_raw, mbar, cbar);
-}
-
 // --------------------------------------------------------------- y-pass ----
 // Partial norms: each thread sums its sites' |psi|^2 in the pass's precision
 // (a few dozen sites), the CTA then adds the threads' sums in FP64.
+// phase: as for the x-pass.
 template <int MODE, typename C, int M>
 __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar,
-                                           double* wsum, uint64_t* cbar)
+                                           double* wsum, uint64_t* cbar, int* phase = nullptr)
 {
     typedef typename RealOf<C>::type R;
     const LineTiling& T = A.t;
@@ -1216,10 +1199,12 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
     constexpr bool in_place = M > 0 || sizeof(C) == 16;
     bool ok = true;
     if (T.bulk && Ll > 0) {
+        const int ph = phase ? *phase : -1;
         if constexpr (in_place)
-            ok = stage_chunks(sa, A.in, plane, line0, nl, L, k0, Ll, T.m, T.cs, T.Lp, &mbar, A.err);
+            ok = stage_chunks(sa, A.in, plane, line0, nl, L, k0, Ll, T.m, T.cs, T.Lp, &mbar, A.err, ph);
         else
-            ok = stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, Ll, &mbar, A.err);
+            ok = stage_rows(sb, A.in, plane, line0, nl, L, k0, Ll, Ll, &mbar, A.err, ph);
+        if (phase) *phase = ok ? ph + 1 : -1;
     }
 
     const FastDiv div_len(Ll), div_nl(nl);
@@ -1346,31 +1331,81 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) ypass_kernel_reg(
     ypass_body<MODE, C, M>(A, blockIdx.x, smem_raw, mbar, wsum, cbar);
 }
 
-template <int MODE, typename C>
-__global__ void __launch_bounds__(512) ypass_batched(const PassArgsT<C>* args, const int2* items, const int* n_items)
+// ------------------------------------------------------- batched passes ----
+// Many instances in one launch, over work items (instance, cta) of the pass.
+// work == null: CTA b runs item b (the grid is the list's capacity; CTAs past
+// *n_items exit at once).  Otherwise the launch is persistent: at most one CTA
+// per resident slot, each taking the next item from the counter work[0] until
+// the list is exhausted; the last CTA to finish resets work[0..1] to zero for
+// the next launch.  Either way an item runs the single-instance pass body with
+// its instance's tiling, so its results do not depend on the launch form.
+template <bool X, int MODE, typename C, int M>
+__device__ __forceinline__ void batched_items(const PassArgsT<C>* args, const int2* items, const int* n_items,
+                                              int* work)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
     __shared__ uint64_t cbar[2];
     __shared__ double wsum[32];
-    if ((int)blockIdx.x >= *n_items) return;
-    const int2 it = items[blockIdx.x];
-    const PassArgsT<C> A = args[it.x];
-    ypass_body<MODE, C, 0>(A, it.y, smem_raw, mbar, wsum, cbar);
+    __shared__ int next;
+    const int n = *n_items;
+    // one inlined body for both forms: phase -1 makes it initialise the barrier
+    int phase = -1, b = blockIdx.x;
+    if (work) {
+        if (threadIdx.x == 0) {
+            mbar_init(&mbar, 1);
+            next = atomicAdd(work, 1);
+        }
+        phase = 0;
+        __syncthreads();  // publishes the first item and the barrier initialisation
+        b = next;
+    }
+    for (;;) {
+        if (b >= n) break;
+        // the next item is taken now and read after this one: the counter's
+        // round trip overlaps the item's work
+        int take = 0;
+        if (work && threadIdx.x == 0) take = atomicAdd(work, 1);
+        const int2 it = items[b];
+        const PassArgsT<C> A = args[it.x];
+        if constexpr (X)
+            xpass_body<MODE, C, M>(A, it.y, smem_raw, mbar, cbar, nullptr, &phase);
+        else
+            ypass_body<MODE, C, M>(A, it.y, smem_raw, mbar, wsum, cbar, &phase);
+        if (!work) return;
+        // this item's shared-memory writes come before the next item's bulk copies
+        // into the same bytes (generic proxy before async proxy)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (threadIdx.x == 0) next = take;
+        __syncthreads();
+        // a staging wait gave up (status bit 8): leave the barrier unused (the item
+        // taken last is not run; the instance's status reports the failure)
+        if (phase < 0) break;
+        b = next;
+    }
+    if (work && threadIdx.x == 0) {
+        __threadfence();  // this CTA's last take from work[0] comes before its count below
+        if (atomicAdd(work + 1, 1) == (int)gridDim.x - 1) {
+            work[0] = 0;
+            work[1] = 0;
+        }
+    }
 }
 
-template <int MODE, typename C, int M>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
-    ypass_batched_reg(const PassArgsT<C>* args, const int2* items, const int* n_items)
+// shared-memory solve (complex128; complex64 tilings with two line arrays)
+template <bool X, int MODE, typename C>
+__global__ void __launch_bounds__(512) pass_batched(const PassArgsT<C>* args, const int2* items, const int* n_items,
+                                                    int* work)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t mbar;
-    __shared__ uint64_t cbar[2];
-    __shared__ double wsum[32];
-    if ((int)blockIdx.x >= *n_items) return;
-    const int2 it = items[blockIdx.x];
-    const PassArgsT<C> A = args[it.x];
-    ypass_body<MODE, C, M>(A, it.y, smem_raw, mbar, wsum, cbar);
+    batched_items<X, MODE, C, 0>(args, items, n_items, work);
+}
+
+// register-resident solve: every item's tiling is a one-array tiling of chunk length M
+template <bool X, int MODE, typename C, int M>
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
+    pass_batched_reg(const PassArgsT<C>* args, const int2* items, const int* n_items, int* work)
+{
+    batched_items<X, MODE, C, M>(args, items, n_items, work);
 }
 
 // ------------------------------------------------------------- launchers ---
@@ -1483,68 +1518,109 @@ int launch_ypass(const PassArgsF& a, int mode, cudaStream_t st)
     return mode == 1 ? launch_line_pass<false, 1>(a, st) : launch_line_pass<false, 0>(a, st);
 }
 
-// Batched launches: grid = capacity items (CTAs past *n_items exit at once),
-// threads and dynamic shared memory the maximum over the batch's instances.
+// Resident CTAs per SM of a batched kernel at the launch's threads and dynamic
+// shared memory (cached: a tick issues the same few launch shapes many times).
+template <typename K>
+static int resident_slots(K kernel, int threads, size_t smem)
+{
+    struct Entry {
+        const void* k;
+        int threads;
+        size_t smem;
+        int slots;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : cache)
+        if (e.k == (const void*)kernel && e.threads == threads && e.smem == smem) return e.slots;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess)
+        return -1;
+    const int slots = std::max(1, per_sm) * sms;
+    cache.push_back(Entry{(const void*)kernel, threads, smem, slots});
+    return slots;
+}
+
+// Batched launches: threads and dynamic shared memory the maximum over the
+// batch's instances.  work == null: grid = capacity items (CTAs past *n_items
+// exit at once); otherwise persistent, grid = min(capacity, resident slots,
+// max_ctas if > 0).
 template <typename C, typename K>
 static int launch_batched_t(K kernel, const PassArgsT<C>* args, const int2* items, const int* n_items, int capacity,
-                            int threads, size_t smem, cudaStream_t st)
+                            int threads, size_t smem, int* work, int max_ctas, cudaStream_t st)
 {
     if (capacity <= 0) return 0;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return report_cuda(e, "cudaFuncSetAttribute(batched pass)");
     }
-    kernel<<<capacity, threads, smem, st>>>(args, items, n_items);
+    int grid = capacity;
+    if (work) {
+        const int slots = resident_slots(kernel, threads, smem);
+        if (slots < 0) return report_cuda(cudaGetLastError(), "occupancy of a batched pass");
+        grid = std::min(capacity, slots);
+        if (max_ctas > 0) grid = std::min(grid, max_ctas);
+    }
+    kernel<<<grid, threads, smem, st>>>(args, items, n_items, work);
     return report_cuda(cudaGetLastError(), "batched pass launch");
 }
 
-int launch_xpass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st, int m_reg)
+template <bool X, int MODE, typename C>
+static int launch_batched_m(const PassArgsT<C>* args, const int2* items, const int* n_items, int capacity,
+                            int threads, size_t smem, int* work, int max_ctas, cudaStream_t st, int m_reg)
 {
-    if (m_reg) return GP_ERR_ARG;  // complex128 tilings use the shared-memory solve
-    return mode == 1 ? launch_batched_t(xpass_batched<1, double2>, args, items, n_items, capacity, threads, smem, st)
-                     : launch_batched_t(xpass_batched<0, double2>, args, items, n_items, capacity, threads, smem, st);
-}
-
-int launch_ypass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st, int m_reg)
-{
-    if (m_reg) return GP_ERR_ARG;
-    return mode == 1 ? launch_batched_t(ypass_batched<1, double2>, args, items, n_items, capacity, threads, smem, st)
-                     : launch_batched_t(ypass_batched<0, double2>, args, items, n_items, capacity, threads, smem, st);
-}
-
-template <bool X, int MODE>
-static int launch_batched_f32(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                              size_t smem, cudaStream_t st, int m_reg)
-{
-#define GP_BATCHED(M)                                                                                              \
-    (X ? launch_batched_t(xpass_batched_reg<MODE, float2, M>, args, items, n_items, capacity, threads, smem, st) \
-       : launch_batched_t(ypass_batched_reg<MODE, float2, M>, args, items, n_items, capacity, threads, smem, st))
-    switch (m_reg) {
-    case 0:
-        return X ? launch_batched_t(xpass_batched<MODE, float2>, args, items, n_items, capacity, threads, smem, st)
-                 : launch_batched_t(ypass_batched<MODE, float2>, args, items, n_items, capacity, threads, smem, st);
-    case 16: return GP_BATCHED(16);
-    case 24: return GP_BATCHED(24);
-    case 32: return GP_BATCHED(32);
-    default: return GP_ERR_ARG;
+#define GP_BATCHED(M)                                                                                           \
+    launch_batched_t(pass_batched_reg<X, MODE, C, M>, args, items, n_items, capacity, threads, smem, work, max_ctas, \
+                     st)
+    if (m_reg == 0)
+        return launch_batched_t(pass_batched<X, MODE, C>, args, items, n_items, capacity, threads, smem, work,
+                                max_ctas, st);
+    if constexpr (sizeof(C) == sizeof(float2)) {  // the register-resident solve is complex64 only
+        switch (m_reg) {
+        case 16: return GP_BATCHED(16);
+        case 24: return GP_BATCHED(24);
+        case 32: return GP_BATCHED(32);
+        default: break;
+        }
     }
+    return GP_ERR_ARG;
 #undef GP_BATCHED
 }
 
-int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st, int m_reg)
+int launch_xpass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st, int m_reg, int* work, int max_ctas)
 {
-    return mode == 1 ? launch_batched_f32<true, 1>(args, items, n_items, capacity, threads, smem, st, m_reg)
-                     : launch_batched_f32<true, 0>(args, items, n_items, capacity, threads, smem, st, m_reg);
+    if (m_reg) return GP_ERR_ARG;  // complex128 tilings use the shared-memory solve
+    return mode == 1
+               ? launch_batched_m<true, 1>(args, items, n_items, capacity, threads, smem, work, max_ctas, st, 0)
+               : launch_batched_m<true, 0>(args, items, n_items, capacity, threads, smem, work, max_ctas, st, 0);
+}
+
+int launch_ypass_batched(const PassArgs* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st, int m_reg, int* work, int max_ctas)
+{
+    if (m_reg) return GP_ERR_ARG;
+    return mode == 1
+               ? launch_batched_m<false, 1>(args, items, n_items, capacity, threads, smem, work, max_ctas, st, 0)
+               : launch_batched_m<false, 0>(args, items, n_items, capacity, threads, smem, work, max_ctas, st, 0);
+}
+
+int launch_xpass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
+                         size_t smem, int mode, cudaStream_t st, int m_reg, int* work, int max_ctas)
+{
+    return mode == 1
+               ? launch_batched_m<true, 1>(args, items, n_items, capacity, threads, smem, work, max_ctas, st, m_reg)
+               : launch_batched_m<true, 0>(args, items, n_items, capacity, threads, smem, work, max_ctas, st, m_reg);
 }
 
 int launch_ypass_batched(const PassArgsF* args, const int2* items, const int* n_items, int capacity, int threads,
-                         size_t smem, int mode, cudaStream_t st, int m_reg)
+                         size_t smem, int mode, cudaStream_t st, int m_reg, int* work, int max_ctas)
 {
-    return mode == 1 ? launch_batched_f32<false, 1>(args, items, n_items, capacity, threads, smem, st, m_reg)
-                     : launch_batched_f32<false, 0>(args, items, n_items, capacity, threads, smem, st, m_reg);
+    return mode == 1
+               ? launch_batched_m<false, 1>(args, items, n_items, capacity, threads, smem, work, max_ctas, st, m_reg)
+               : launch_batched_m<false, 0>(args, items, n_items, capacity, threads, smem, work, max_ctas, st, m_reg);
 }
 
 }  // namespace gpspin

@@ -36,7 +36,8 @@ EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_s
            "gp_init_winding", "gp_set_magnetization", "gp_set_splitting", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
            "gp_tiling_info", "gp_set_tiling", "gp_plan_tiling", "gp_check_wait_timeout",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
-           "gp_batch_step", "gp_batch_poll", "gp_batch_use_graphs", "gp_batch_set_running_limit", "gp_batch_set_queue_limit", "gp_batch_cancel", "gp_batch_error",
+           "gp_batch_step", "gp_batch_poll", "gp_batch_use_graphs", "gp_batch_set_persistent", "gp_batch_set_running_limit",
+           "gp_batch_set_queue_limit", "gp_batch_cancel", "gp_batch_error",
            "gp_inject_alloc_failure", "gp_checkpoint_bytes", "gp_checkpoint_save", "gp_checkpoint_load",
            "gp_strerror"]
 
@@ -179,11 +180,13 @@ def load():
                                   ctypes.POINTER(Obs), dp, ip]
     lib.gp_batch_set_queue_limit.argtypes = [vp, ip]
     lib.gp_batch_use_graphs.argtypes = [vp, ip]
+    lib.gp_batch_set_persistent.argtypes = [vp, ip]
     lib.gp_batch_set_running_limit.argtypes = [vp, ctypes.c_longlong]
     lib.gp_batch_set_running_limit.restype = ctypes.c_int
     lib.gp_batch_cancel.argtypes = [vp, ctypes.c_longlong]
     lib.gp_batch_error.argtypes = [vp, ctypes.c_longlong]
-    for name in ("gp_batch_create", "gp_batch_submit", "gp_batch_step", "gp_batch_poll", "gp_batch_use_graphs", "gp_batch_set_running_limit", "gp_batch_set_queue_limit",
+    for name in ("gp_batch_create", "gp_batch_submit", "gp_batch_step", "gp_batch_poll", "gp_batch_use_graphs",
+                 "gp_batch_set_persistent", "gp_batch_set_running_limit", "gp_batch_set_queue_limit",
                  "gp_batch_cancel", "gp_batch_error"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gp_inject_alloc_failure.argtypes = [ctypes.c_longlong]
@@ -472,6 +475,13 @@ class Batch:
     def use_graphs(self, enable=True):
         """Replay captured ticks while the running set is unchanged (default) or launch directly."""
         _check(load().gp_batch_use_graphs(self._b, int(bool(enable))), "gp_batch_use_graphs")
+
+    def set_persistent(self, max_ctas=0):
+        """Batched launch form: 0 persistent, one CTA per resident slot, CTAs taking the work items
+        from a counter; > 0 the same with at most max_ctas CTAs; None or < 0 one CTA per work item
+        (the batch's default)."""
+        v = -1 if max_ctas is None else int(max_ctas)
+        _check(load().gp_batch_set_persistent(self._b, v), "gp_batch_set_persistent")
 
     def set_running_limit(self, max_sites):
         """Admit while the running solves' grid points stay within max_sites (0: no limit)."""

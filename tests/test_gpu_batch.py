@@ -25,11 +25,13 @@ def req_params(n, **kw):
     return p
 
 
-def run_batch(items, max_bytes=8 << 30, graphs=True):
+def run_batch(items, max_bytes=8 << 30, graphs=True, persist=None):
     """items: list of (params, submit kwargs); runs until all are done."""
     out = {}
     with gpspin.Batch(max_bytes, check_every=CHECK) as b:
         b.use_graphs(graphs)
+        if persist is not None:
+            b.set_persistent(persist)
         ids = [b.submit(p, **kw) for p, kw in items]
         for _ in range(10000):
             nr, nq = b.step()
@@ -121,6 +123,29 @@ def test_graph_ticks_equal_direct_ticks_bitwise():
     for x, y in zip(a, b):
         assert x[0] == y[0] == gpspin.REQ_DONE and x[1] == y[1]
         assert np.array_equal(x[3], y[3])
+
+
+def test_persistent_launches_equal_one_cta_per_item_bitwise():
+    """Persistent batched launches (CTAs taking the work items from a device
+    counter, largest grids first) give bitwise the results of one CTA per work
+    item: at one CTA per resident slot, and with the grid capped at a few CTAs
+    so that every CTA runs many items and many phases of its staging barrier
+    (and the counter is reset between the launches of a tick), with graph and
+    direct ticks, both precision groups and a running set that changes."""
+    items = [
+        (req_params(64, c2=12.0, so_type=2), dict(seed=3, tol=1e-300, cap=60)),
+        (req_params(96), dict(seed=11, tol=1e-300, cap=140)),
+        (req_params(128, omeg=0.8), dict(seed=5, tol=1e-300, cap=100, policy=gpspin.POLICY_FP32_REFINE,
+                                         refine_steps=40)),
+        (req_params(80, rabi=0.0), dict(seed=9, tol=1e-300, cap=80, policy=gpspin.POLICY_FP32_REFINE,
+                                        refine_steps=20)),
+    ]
+    ref = run_batch(items, graphs=False, persist=-1)
+    for graphs, persist in ((True, 0), (False, 5), (True, 3)):
+        got = run_batch(items, graphs=graphs, persist=persist)
+        for x, y in zip(ref, got):
+            assert x[0] == y[0] == gpspin.REQ_DONE and x[1] == y[1]
+            assert np.array_equal(x[3], y[3])
 
 
 def test_running_limit_admits_by_work_in_flight():
