@@ -337,10 +337,11 @@ __global__ void trap_table_kernel(C* out, int n, double len, double w, double dt
 // with t = sqrt(u); both are power series in u, used directly: three terms for
 // u <= 1e-4 and five for u <= 1/100 (first omitted term <= 2.5e-18 relative).
 // The scalar factor exp(-tau' c0 rho) is a Taylor series: eight terms (imaginary
-// time) or four plus four (cos, sin in real time) for dt c0 rho <= 1/64, and
+// time) or four plus four (cos, sin in real time) for |dt c0 rho| <= 1/64, and
 // eleven/twelve terms up to 1/8 (<= 3e-18); larger arguments take the library
-// exp / sincos.  The trap factor comes from
-// the per-axis tables.  The complex64 version evaluates the same formulas in
+// exp / sincos.  The tiers test |x|: an attractive contact interaction (c0 < 0)
+// makes the argument negative, and the truncation bounds depend on |x| only.
+// The trap factor comes from the per-axis tables.  The complex64 version evaluates the same formulas in
 // FP32 (three-term series for u <= 1/100, library expf / sincosf otherwise).
 template <typename R>
 struct PConstT {
@@ -416,15 +417,16 @@ __device__ __forceinline__ void spin_series(float u, float& s1, float& s2)
     }
 }
 
-// e^{-x} (imaginary time) and cos x, sin x (real time) of x = dt c0 rho >= 0.
+// e^{-x} (imaginary time) and cos x, sin x (real time) of x = dt c0 rho, of
+// either sign (c0 < 0 is an attractive interaction).
 __device__ __forceinline__ double scalar_exp(double x)
 {
-    const double mx = -x;
-    if (x <= 0.015625) {
-        // eight terms for x <= 1/64: the first omitted one is x^8/8! <= 1.7e-19
+    const double mx = -x, ax = fabs(x);
+    if (ax <= 0.015625) {
+        // eight terms for |x| <= 1/64: the first omitted one is |x|^8/8! <= 1.7e-19
         return fma(fma(fma(fma(fma(fma(fma(mx, 1.0 / 5040.0, 1.0 / 720.0), mx, 1.0 / 120.0), mx, 1.0 / 24.0), mx,
                                 1.0 / 6.0), mx, 0.5), mx, 1.0), mx, 1.0);
-    } else if (x <= 0.125) {
+    } else if (ax <= 0.125) {
         double e = fma(fma(fma(fma(fma(fma(fma(fma(fma(fma(mx, 1.0 / 39916800.0, 1.0 / 3628800.0), mx, 1.0 / 362880.0),
                                                    mx, 1.0 / 40320.0), mx, 1.0 / 5040.0), mx, 1.0 / 720.0),
                                        mx, 1.0 / 120.0), mx, 1.0 / 24.0), mx, 1.0 / 6.0), mx, 0.5), mx, 1.0);
@@ -436,12 +438,13 @@ __device__ __forceinline__ float scalar_exp(float x) { return expf(-x); }
 
 __device__ __forceinline__ void scalar_cis(double x, double& cs, double& sn)
 {
-    if (x <= 0.015625) {
-        // x <= 1/64: the first omitted terms x^8/8! and x^9/9! are <= 1e-19
+    const double ax = fabs(x);
+    if (ax <= 0.015625) {
+        // |x| <= 1/64: the first omitted terms |x|^8/8! and |x|^9/9! are <= 1e-19
         double x2 = x * x;
         cs = fma(fma(fma(x2, -1.0 / 720.0, 1.0 / 24.0), x2, -0.5), x2, 1.0);
         sn = x * fma(fma(fma(x2, -1.0 / 5040.0, 1.0 / 120.0), x2, -1.0 / 6.0), x2, 1.0);
-    } else if (x <= 0.125) {
+    } else if (ax <= 0.125) {
         double x2 = x * x;
         cs = fma(fma(fma(fma(fma(x2, -1.0 / 3628800.0, 1.0 / 40320.0), x2, -1.0 / 720.0), x2, 1.0 / 24.0), x2, -0.5),
                  x2, 1.0);
@@ -1340,8 +1343,34 @@ __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) ypass_kernel_reg(
 // the next launch.  Either way an item runs the single-instance pass body with
 // its instance's tiling, so its results do not depend on the launch form.
 template <bool X, int MODE, typename C, int M>
-__device__ __forceinline__ void batched_items(const PassArgsT<C>* args, const int2* items, const int* n_items,
-                                              int* work)
+__device__ __forceinline__ void batched_item(const PassArgsT<C>& A, int cta, unsigned char* smem_raw, uint64_t& mbar,
+                                             uint64_t* cbar, double* wsum, int* phase)
+{
+    if constexpr (X)
+        xpass_body<MODE, C, M>(A, cta, smem_raw, mbar, cbar, nullptr, phase);
+    else
+        ypass_body<MODE, C, M>(A, cta, smem_raw, mbar, wsum, cbar, phase);
+}
+
+// One CTA per work item (the grid is the list's capacity; CTAs past *n_items exit at once).
+template <bool X, int MODE, typename C, int M>
+__device__ __forceinline__ void batched_one(const PassArgsT<C>* args, const int2* items, const int* n_items)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t mbar;
+    __shared__ uint64_t cbar[2];
+    __shared__ double wsum[32];
+    if ((int)blockIdx.x >= *n_items) return;
+    const int2 it = items[blockIdx.x];
+    const PassArgsT<C> A = args[it.x];
+    batched_item<X, MODE, C, M>(A, it.y, smem_raw, mbar, cbar, wsum, nullptr);
+}
+
+// Persistent: each CTA takes items from the counter work[0] until the list is
+// exhausted; the last CTA to finish resets work[0..1] to zero for the next launch.
+template <bool X, int MODE, typename C, int M>
+__device__ __forceinline__ void batched_loop(const PassArgsT<C>* args, const int2* items, const int* n_items,
+                                             int* work)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
@@ -1349,30 +1378,21 @@ __device__ __forceinline__ void batched_items(const PassArgsT<C>* args, const in
     __shared__ double wsum[32];
     __shared__ int next;
     const int n = *n_items;
-    // one inlined body for both forms: phase -1 makes it initialise the barrier
-    int phase = -1, b = blockIdx.x;
-    if (work) {
-        if (threadIdx.x == 0) {
-            mbar_init(&mbar, 1);
-            next = atomicAdd(work, 1);
-        }
-        phase = 0;
-        __syncthreads();  // publishes the first item and the barrier initialisation
-        b = next;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        next = atomicAdd(work, 1);
     }
-    for (;;) {
-        if (b >= n) break;
+    int phase = 0;
+    __syncthreads();  // publishes the first item and the barrier initialisation
+    int b = next;
+    while (b < n) {
         // the next item is taken now and read after this one: the counter's
         // round trip overlaps the item's work
         int take = 0;
-        if (work && threadIdx.x == 0) take = atomicAdd(work, 1);
+        if (threadIdx.x == 0) take = atomicAdd(work, 1);
         const int2 it = items[b];
         const PassArgsT<C> A = args[it.x];
-        if constexpr (X)
-            xpass_body<MODE, C, M>(A, it.y, smem_raw, mbar, cbar, nullptr, &phase);
-        else
-            ypass_body<MODE, C, M>(A, it.y, smem_raw, mbar, wsum, cbar, &phase);
-        if (!work) return;
+        batched_item<X, MODE, C, M>(A, it.y, smem_raw, mbar, cbar, wsum, &phase);
         // this item's shared-memory writes come before the next item's bulk copies
         // into the same bytes (generic proxy before async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1383,7 +1403,7 @@ __device__ __forceinline__ void batched_items(const PassArgsT<C>* args, const in
         if (phase < 0) break;
         b = next;
     }
-    if (work && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         __threadfence();  // this CTA's last take from work[0] comes before its count below
         if (atomicAdd(work + 1, 1) == (int)gridDim.x - 1) {
             work[0] = 0;
@@ -1394,18 +1414,31 @@ __device__ __forceinline__ void batched_items(const PassArgsT<C>* args, const in
 
 // shared-memory solve (complex128; complex64 tilings with two line arrays)
 template <bool X, int MODE, typename C>
-__global__ void __launch_bounds__(512) pass_batched(const PassArgsT<C>* args, const int2* items, const int* n_items,
-                                                    int* work)
+__global__ void __launch_bounds__(512) pass_batched(const PassArgsT<C>* args, const int2* items, const int* n_items)
 {
-    batched_items<X, MODE, C, 0>(args, items, n_items, work);
+    batched_one<X, MODE, C, 0>(args, items, n_items);
+}
+
+template <bool X, int MODE, typename C>
+__global__ void __launch_bounds__(512) pass_persistent(const PassArgsT<C>* args, const int2* items,
+                                                       const int* n_items, int* work)
+{
+    batched_loop<X, MODE, C, 0>(args, items, n_items, work);
 }
 
 // register-resident solve: every item's tiling is a one-array tiling of chunk length M
 template <bool X, int MODE, typename C, int M>
 __global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
-    pass_batched_reg(const PassArgsT<C>* args, const int2* items, const int* n_items, int* work)
+    pass_batched_reg(const PassArgsT<C>* args, const int2* items, const int* n_items)
 {
-    batched_items<X, MODE, C, M>(args, items, n_items, work);
+    batched_one<X, MODE, C, M>(args, items, n_items);
+}
+
+template <bool X, int MODE, typename C, int M>
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
+    pass_persistent_reg(const PassArgsT<C>* args, const int2* items, const int* n_items, int* work)
+{
+    batched_loop<X, MODE, C, M>(args, items, n_items, work);
 }
 
 // ------------------------------------------------------------- launchers ---
@@ -1544,39 +1577,41 @@ static int resident_slots(K kernel, int threads, size_t smem)
 }
 
 // Batched launches: threads and dynamic shared memory the maximum over the
-// batch's instances.  work == null: grid = capacity items (CTAs past *n_items
-// exit at once); otherwise persistent, grid = min(capacity, resident slots,
-// max_ctas if > 0).
-template <typename C, typename K>
-static int launch_batched_t(K kernel, const PassArgsT<C>* args, const int2* items, const int* n_items, int capacity,
-                            int threads, size_t smem, int* work, int max_ctas, cudaStream_t st)
+// batch's instances.  work == null: kernel `one`, grid = capacity items (CTAs
+// past *n_items exit at once); otherwise kernel `loop`, persistent, grid =
+// min(capacity, resident slots, max_ctas if > 0).
+template <typename C, typename K1, typename KP>
+static int launch_batched_t(K1 one, KP loop, const PassArgsT<C>* args, const int2* items, const int* n_items,
+                            int capacity, int threads, size_t smem, int* work, int max_ctas, cudaStream_t st)
 {
     if (capacity <= 0) return 0;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = work ? cudaFuncSetAttribute(loop, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                             : cudaFuncSetAttribute(one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return report_cuda(e, "cudaFuncSetAttribute(batched pass)");
     }
-    int grid = capacity;
-    if (work) {
-        const int slots = resident_slots(kernel, threads, smem);
-        if (slots < 0) return report_cuda(cudaGetLastError(), "occupancy of a batched pass");
-        grid = std::min(capacity, slots);
-        if (max_ctas > 0) grid = std::min(grid, max_ctas);
+    if (!work) {
+        one<<<capacity, threads, smem, st>>>(args, items, n_items);
+        return report_cuda(cudaGetLastError(), "batched pass launch");
     }
-    kernel<<<grid, threads, smem, st>>>(args, items, n_items, work);
-    return report_cuda(cudaGetLastError(), "batched pass launch");
+    const int slots = resident_slots(loop, threads, smem);
+    if (slots < 0) return report_cuda(cudaGetLastError(), "occupancy of a batched pass");
+    int grid = std::min(capacity, slots);
+    if (max_ctas > 0) grid = std::min(grid, max_ctas);
+    loop<<<grid, threads, smem, st>>>(args, items, n_items, work);
+    return report_cuda(cudaGetLastError(), "persistent batched pass launch");
 }
 
 template <bool X, int MODE, typename C>
 static int launch_batched_m(const PassArgsT<C>* args, const int2* items, const int* n_items, int capacity,
                             int threads, size_t smem, int* work, int max_ctas, cudaStream_t st, int m_reg)
 {
-#define GP_BATCHED(M)                                                                                           \
-    launch_batched_t(pass_batched_reg<X, MODE, C, M>, args, items, n_items, capacity, threads, smem, work, max_ctas, \
-                     st)
+#define GP_BATCHED(M)                                                                                          \
+    launch_batched_t(pass_batched_reg<X, MODE, C, M>, pass_persistent_reg<X, MODE, C, M>, args, items, n_items, \
+                     capacity, threads, smem, work, max_ctas, st)
     if (m_reg == 0)
-        return launch_batched_t(pass_batched<X, MODE, C>, args, items, n_items, capacity, threads, smem, work,
-                                max_ctas, st);
+        return launch_batched_t(pass_batched<X, MODE, C>, pass_persistent<X, MODE, C>, args, items, n_items,
+                                capacity, threads, smem, work, max_ctas, st);
     if constexpr (sizeof(C) == sizeof(float2)) {  // the register-resident solve is complex64 only
         switch (m_reg) {
         case 16: return GP_BATCHED(16);

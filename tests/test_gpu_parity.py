@@ -64,6 +64,21 @@ def test_substep_parity_large_arguments(mode):
 
 
 @pytest.mark.parametrize("mode", [IMAG, REAL])
+@pytest.mark.parametrize("c0", [-3.0, -25.0, -300.0])
+def test_substep_parity_attractive_contact(c0, mode):
+    # c0 < 0 (attractive): dt c0 rho is negative, and its magnitude falls in each
+    # tier of the scalar factor in turn (|x| <= 1/64, <= 1/8, beyond) somewhere on the grid
+    p = ragged(c0=c0, dt=0.01)
+    psi = smooth_plus_rough(p, 13)
+    want = oracle.substep(p, psi, "P", mode)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        s.apply_substep("P", mode)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("mode", [IMAG, REAL])
 def test_short_run_parity(mode):
     p = ragged()
     psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=5)
