@@ -117,7 +117,8 @@ def parse():
                     help="serving: grid points of the solves running at once (0: admit by memory only)")
     ap.add_argument("--no-autotune", action="store_true", help="time the default tiling instead of the tuned one")
     ap.add_argument("--tiling", default=None,
-                    help="S,R,m: cluster size, lines per CTA and chunk length of both passes (instead of autotuning)")
+                    help="S,R,m[,reg|smem]: cluster size, lines per CTA, chunk length and solve kind of both passes "
+                         "(instead of autotuning); X:Y gives the x-pass and the y-pass their own")
     ap.add_argument("--substeps", action="store_true",
                     help="time split of the passes: the x- and y-pass with only P, only the X solve, only the Y "
                          "solve, then one full step (NVTX range 'substeps'); prints one JSON line")
@@ -239,7 +240,7 @@ def kernel_name(dom, mode, prec, tiles, strang):
     if strang and dom == "xpass":
         return f"xpass_kernel<{mode}, double2> + xtail_kernel<{mode}> (both x-passes of a second-order step)"
     if td.get("register_solve"):
-        return f"{dom}_kernel_reg<{mode}, float2, {td['chunk']}>"
+        return f"{dom}_kernel_reg<{mode}, {'float2' if prec == 'fp32' else 'double2'}, {td['chunk']}>"
     return f"{dom}_kernel<{mode}, {'float2' if prec == 'fp32' else 'double2'}>"
 
 
@@ -311,9 +312,12 @@ def prepare(name, prec, stream, args, main=True):
         s.set_magnetization(args.magnetization)
     tuned_ms = None
     if args.tiling:
-        S, R, m = (int(v) for v in args.tiling.split(","))
+        specs = args.tiling.split(":")
         for d in (0, 1):
-            s.set_tiling(d, cluster=S, lines_per_cta=R, chunk=m, mode=mode)
+            f = specs[min(d, len(specs) - 1)].split(",")
+            kind = {"reg": True, "smem": False}[f[3]] if len(f) > 3 else None
+            s.set_tiling(d, cluster=int(f[0]), lines_per_cta=int(f[1]), chunk=int(f[2]), mode=mode,
+                         register_solve=kind)
     elif not args.no_autotune:
         tuned_ms = s.autotune(mode)  # the state is unchanged
     return s, c, p, mode, prep_steps, tuned_ms

@@ -289,29 +289,39 @@ int gp_batch_step(gp_batch* b, int* n_running, int* n_queued);
 int gp_batch_poll(gp_batch* b, long long id, int* state, long long* steps, gp_obs* obs, double* psi_out, int release);
 
 /* Autotuner: for the handle's current precision and the given mode, times the
- * x-pass and the y-pass for each candidate tiling -- lines per CTA (1, 2, 4),
- * one CTA or a cluster of 2, 4 or 8 CTAs per line group, chunk lengths of the parallel
- * Thomas solve -- on the handle's stream, and keeps the fastest for later
- * propagation.  The state is saved and restored, so tuning does not change the
- * solve; results stay within the parity tolerances (only the summation order of
- * partial norms and the chunking change).  *ms_out (may be NULL) receives the
- * tuned x-pass + y-pass time.  Allocates one temporary copy of psi. */
+ * x-pass and the y-pass for each candidate tiling -- lines per CTA (1, 2, 4, 8),
+ * one CTA or a cluster of 2, 4 or 8 CTAs per line group, chunk lengths of the
+ * parallel Thomas solve, and for complex128 the shared-memory and the
+ * register-resident solve -- on the handle's stream, and keeps the fastest for
+ * later propagation.  Each candidate is timed as the best of three launches,
+ * each started from a cold L2 (a scratch buffer of 1.5 x the L2 size is
+ * written first; from a warm L2 if that buffer cannot be allocated).  The
+ * state is saved and restored, so tuning does not change the solve; results
+ * stay within the parity tolerances (only the summation order of partial
+ * norms and the chunking change).  *ms_out (may be NULL) receives the tuned
+ * x-pass + y-pass time.  Allocates one temporary copy of psi and the scratch
+ * buffer, both freed before it returns. */
 int gp_autotune(gp_handle* h, int mode, double* ms_out);
 
 /* Sets the tiling of one pass (dir 0: x-pass, 1: y-pass) for the handle's current
  * precision and the given mode: cluster = CTAs per line group (1, 2, 4 or 8),
  * lines_per_cta, chunk = minimum chunk length of the parallel Thomas solve
- * (raised to what the precision needs).  GP_ERR_ARG or GP_ERR_UNSUPPORTED if
- * the tiling does not fit (threads, shared memory, chunks per CTA).  Results
- * stay within the parity tolerances for every valid tiling. */
-int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk);
+ * (raised to what the precision needs), register_solve = the solve kind:
+ * 1 register-resident chunks (complex64 chunk length 16, 24 or 32; complex128
+ * chunk length 32, at most 384 threads per CTA), 0 shared-memory line arrays,
+ * -1 the precision's default (complex64 register-resident up to chunk length
+ * 32, complex128 shared memory).  GP_ERR_ARG or GP_ERR_UNSUPPORTED if the
+ * tiling does not fit (threads, shared memory, chunks per CTA, chunk length).
+ * Results stay within the parity tolerances for every valid tiling. */
+int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk, int register_solve);
 
 /* The tiling the handle uses for a pass (dir 0: x-pass, 1: y-pass) in the given
  * mode and its current precision: out[0] CTAs per line group (cluster size),
  * out[1] lines per CTA, out[2] chunk length, out[3] chunks per line, out[4]
  * threads per CTA, out[5] dynamic shared memory bytes, out[6] CTAs per launch,
  * out[7] solve kind: 0 shared-memory line arrays, 1 register-resident chunks
- * (complex64, chunk length 16, 24 or 32).  out must hold 8 ints. */
+ * (complex64 chunk length 16, 24 or 32; complex128 chunk length 32).  out must
+ * hold 8 ints. */
 int gp_tiling_info(gp_handle* h, int mode, int dir, int* out);
 
 /* The default tiling of a pass (dir 0: x-pass, 1: y-pass) for these parameters

@@ -120,8 +120,8 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
 {
     if (!(cpmax < 0.5)) return GP_ERR_UNSUPPORTED;
     if (S < 1 || S > 8 || (S & (S - 1)) || R < 1) return GP_ERR_ARG;  // portable cluster sizes
-    if (kind < TILE_C128 || kind > TILE_C64_REG) return GP_ERR_ARG;
-    const bool c64 = kind != TILE_C128;
+    if (kind < TILE_C128 || kind > TILE_C128_REG) return GP_ERR_ARG;
+    const bool c64 = kind == TILE_C64 || kind == TILE_C64_REG;
     const double bits = c64 ? 26.0 : 60.0;
     const size_t elem = c64 ? sizeof(float2) : sizeof(double2);
     int F = cpmax > 0 ? (int)std::ceil(bits * std::log(2.0) / -std::log(cpmax)) + 1 : 1;
@@ -130,7 +130,11 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
     int m = std::max(std::max(16, H + F), m_req);
     m = (m + 3) / 4 * 4;
     if (kind == TILE_C64_REG && m <= 32) m = m <= 16 ? 16 : (m <= 24 ? 24 : 32);
-    const bool single = kind == TILE_C64_REG && m <= 32;
+    if (kind == TILE_C128_REG) {
+        if (m > 32) return GP_ERR_UNSUPPORTED;  // compiled for m = 32 only
+        m = 32;
+    }
+    const bool single = (kind == TILE_C64_REG && m <= 32) || kind == TILE_C128_REG;
     int Q = (L + m - 1) / m;
     if (S > 1 && Q < 2 * S) return GP_ERR_ARG;  // at least two chunks per CTA
     const int Qc = (Q + S - 1) / S;
@@ -139,7 +143,7 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
     // array the chunks are staged in place by 16-byte bulk copies and the solve
     // moves two complex64 per access: even strides, conflicts counted per
     // 16-byte access (8 per wavefront).
-    const int unit = single ? 2 : 1;
+    const int unit = single && c64 ? 2 : 1;
     const int G = single ? 8 : (c64 ? 16 : 8);
     int cs = m, Lp = Qc * m, best = -1;
     for (int dc = 0; dc < (compact ? 1 : G * unit); dc += unit)
@@ -158,6 +162,8 @@ int make_tiling(int L, int nlines, double cpmax, int kind, int S, int R, int m_r
     // the cluster neighbours push into (register-resident solve)
     const size_t smem = line_bytes * (single ? 1 : 2) + 2 * up(3 * R * Qc * elem) + up(2 * 3 * R * elem);
     if (smem > 227 * 1024) return GP_ERR_UNSUPPORTED;
+    // the complex128 register-resident kernels are compiled for at most 384 threads
+    if (kind == TILE_C128_REG && 3 * R * Qc > 384) return GP_ERR_ARG;
     t->L = L;
     t->nlines = nlines;
     t->R = R;
@@ -972,13 +978,16 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out)
 
 extern "C++" {
 // Times one pass (x: dir 0, y: dir 1) with the given tiling: best of three
-// launches on the handle's stream, in ms (negative if the launch fails).
+// launches on the handle's stream, in ms (negative if the launch fails).  With
+// a flush buffer each timed launch starts from a cold L2 (the buffer, larger
+// than L2, is written first), as in a step whose input has left the cache.
 template <typename A>
-float time_pass(gp_handle* h, A a, int dir, int mode)
+float time_pass(gp_handle* h, A a, int dir, int mode, void* flush, size_t flush_bytes)
 {
     a.partials = nullptr;
     float best = -1.0f;
     for (int rep = 0; rep < 4; ++rep) {
+        if (flush && cudaMemsetAsync(flush, rep, flush_bytes, h->stream) != cudaSuccess) return -1.0f;
         if (cudaEventRecord(h->ev[0], h->stream) != cudaSuccess) return -1.0f;
         int rc = dir == 0 ? launch_xpass(a, mode, h->stream) : launch_ypass(a, mode, h->stream);
         if (rc || cudaEventRecord(h->ev[1], h->stream) != cudaSuccess || cudaEventSynchronize(h->ev[1]) != cudaSuccess)
@@ -1011,6 +1020,20 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
         cudaFree(keep);
         return GP_ERR_CUDA;
     }
+    // scratch larger than L2 for cold-cache timings (warm timings if it does not fit)
+    void* flush = nullptr;
+    size_t flush_bytes = 0;
+    {
+        int dev = 0, l2 = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
+            l2 > 0) {
+            flush_bytes = (size_t)l2 * 3 / 2;
+            if (!dalloc(&flush, flush_bytes)) {
+                flush = nullptr;
+                cudaGetLastError();
+            }
+        }
+    }
     double best_total = 0;
     for (int dir = 0; dir < 2 && st == GP_OK; ++dir) {
         const int L = dir == 0 ? p.nx : p.ny, nl = dir == 0 ? p.ny : p.nx;
@@ -1019,13 +1042,16 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
         LineTiling best = cur;
         float best_ms = -1.0f;
         const int ms_add[] = {0, 4, 8, 16, 32};
+        // complex128: the shared-memory solve and the register-resident one (m = 32)
+        const int kinds[2] = {f32 ? TILE_C64_REG : TILE_C128, TILE_C128_REG};
+        for (int kind : kinds)
         for (int compact : {0, 1})
         for (int S : {1, 2, 4, 8})
             for (int R : {1, 2, 4, 8})
                 for (int add : ms_add) {
+                    if (f32 && kind == TILE_C128_REG) continue;
                     LineTiling t;
-                    if (make_tiling(L, nl, cp, f32 ? TILE_C64_REG : TILE_C128, S, R, cur.m - (cur.m % 4) + add, &t,
-                                    compact) != GP_OK)
+                    if (make_tiling(L, nl, cp, kind, S, R, cur.m - (cur.m % 4) + add, &t, compact) != GP_OK)
                         continue;
                     if (S > 1 && L < 64) continue;
                     float ms;
@@ -1033,12 +1059,12 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
                         PassArgsF a = pass_args_f32(h, cs, dir);
                         t.bulk = a.t.bulk;
                         a.t = t;
-                        ms = time_pass(h, a, dir, mode);
+                        ms = time_pass(h, a, dir, mode, flush, flush_bytes);
                     } else {
                         PassArgs a = pass_args(h, cs, dir);
                         t.bulk = a.t.bulk;
                         a.t = t;
-                        ms = time_pass(h, a, dir, mode);
+                        ms = time_pass(h, a, dir, mode, flush, flush_bytes);
                     }
                     if (ms > 0 && (best_ms < 0 || ms < best_ms)) {
                         best_ms = ms;
@@ -1054,6 +1080,7 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out)
     if (cudaMemcpyAsync(state, keep, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) st = GP_ERR_CUDA;
     cudaStreamSynchronize(h->stream);
     cudaFree(keep);
+    cudaFree(flush);
     drop_graphs(h);
     if (ms_out) *ms_out = best_total;
     return st;
@@ -1084,17 +1111,22 @@ int gp_plan_tiling(const gp_params* p, int mode, int dir, int* out)
     return GP_OK;
 }
 
-int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk)
+int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk, int register_solve)
 {
     if (!h || (mode != GP_IMAG && mode != GP_REAL) || dir < 0 || dir > 1) return GP_ERR_ARG;
+    if (register_solve < -1 || register_solve > 1) return GP_ERR_ARG;
     int st = ensure_coef(h, mode);
     if (st) return st;
     CoefSet& cs = h->coef[mode];
     const gp_params& p = h->p;
     const bool f32 = h->active == GP_FP32_MIXED;
+    const int kind = f32 ? (register_solve == 0 ? TILE_C64 : TILE_C64_REG)
+                         : (register_solve == 1 ? TILE_C128_REG : TILE_C128);
     LineTiling t;
-    st = make_tiling(dir == 0 ? p.nx : p.ny, dir == 0 ? p.ny : p.nx, max_cp(p, dir, mode),
-                     f32 ? TILE_C64_REG : TILE_C128, cluster, lines_per_cta, chunk, &t);
+    st = make_tiling(dir == 0 ? p.nx : p.ny, dir == 0 ? p.ny : p.nx, max_cp(p, dir, mode), kind, cluster,
+                     lines_per_cta, chunk, &t);
+    if (st) return st;
+    if (register_solve == 1 && !t.single) return GP_ERR_UNSUPPORTED;  // chunk longer than the compiled ones
     if (st) return st;
     (f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty)) = t;
     drop_graphs(h);

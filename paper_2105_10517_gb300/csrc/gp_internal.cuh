@@ -72,12 +72,14 @@ struct LineTiling {
     size_t off_cf; // staging area of the bulk row copies) and of the carry arrays
     size_t off_cb;
     int bulk;      // rows are 16-byte aligned: stage them with cp.async.bulk
-    int single;    // one line array: rows are staged in place (complex64 register-resident solve, m = 16/24/32)
+    int single;    // one line array: rows are staged in place (register-resident solve: complex64
+                   // m = 16/24/32, complex128 m = 32)
 };
 
 // Kinds of tiling: complex128; complex64 with the shared-memory solve (two line
-// arrays, any chunk length); complex64 with the register-resident solve.
-enum TileKind { TILE_C128 = 0, TILE_C64 = 1, TILE_C64_REG = 2 };
+// arrays, any chunk length); complex64 with the register-resident solve;
+// complex128 with the register-resident solve (one line array, m = 32).
+enum TileKind { TILE_C128 = 0, TILE_C64 = 1, TILE_C64_REG = 2, TILE_C128_REG = 3 };
 
 template <typename C>
 struct PassArgsT {

@@ -160,6 +160,13 @@ __device__ __forceinline__ void push_carry(float2 v, float2* slot, uint64_t* bar
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(b) : "memory");
 }
 
+__device__ __forceinline__ void push_carry(double2 v, double2* slot, uint64_t* bar, uint32_t rank)
+{
+    const uint32_t a = cluster_map(slot, rank), b = cluster_map(bar, rank);
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(b) : "memory");
+}
+
 __device__ __forceinline__ void wait_carry(uint64_t* bar, int* err)
 {
     uint32_t ok = 0;
@@ -713,13 +720,14 @@ __device__ __forceinline__ ConvCoef<C> load_conv(const LineCoefT<C>* coef, const
 // Chunks q >= 1 start at row m >= H + F, past the rows where the factorisation
 // still differs from its limit (H rows) and where the fixup powers matter, so
 // they use the converged coefficients throughout; chunk 0 takes the table rows.
+// Complex64 moves two points per 16-byte shared-memory access, complex128 one.
 template <int MODE, typename C, int M>
 __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const LineCoefT<C>* coef,
                                                    const ConvCoef<C>& cc, const LineTiling& T, const Part& P,
                                                    C* hf, C* hb, uint64_t* cbar, int* err)
 {
     typedef typename RealOf<C>::type R;
-    static_assert(sizeof(C) == 8 && M % 2 == 0, "pairs of complex64 per 16-byte shared-memory access");
+    static_assert(sizeof(C) == 16 || M % 2 == 0, "pairs of complex64 per 16-byte shared-memory access");
     const int Q = T.Q, F = T.F, L = T.L, Lp = T.Lp, Qc = T.Qc;
     const int nl3 = 3 * max(P.nl, 1);
     const int tid = threadIdx.x;
@@ -736,7 +744,31 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
     const C zero = mkc<C>(R(0), R(0));
     const C inv_c = cc.inv, g_c = cc.g, cp_c = cc.cp;
     C y[M];
-    if (active) {
+    if (active && sizeof(C) == 16) {
+        // complex128: forward elimination from a zero carry, one point per access
+        C v = zero;
+        if (q == 0) {
+#pragma unroll
+            for (int t = 0; t < M; ++t) {
+                const int k = t < kHead - 1 ? t : kHead - 1;
+                v = cfnma(Co->g[k], v, scale_inv<MODE>(Co->inv[k], pa[t]));
+                y[t] = t < len ? v : zero;
+            }
+        } else if (len == M) {
+#pragma unroll
+            for (int t = 0; t < M; ++t) {
+                v = cfnma(g_c, v, scale_inv<MODE>(inv_c, pa[t]));
+                y[t] = v;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < M; ++t) {
+                v = cfnma(g_c, v, scale_inv<MODE>(inv_c, pa[t]));
+                y[t] = t < len ? v : zero;
+            }
+        }
+        cf[lc * Qc + ql] = y[M - 1];
+    } else if (active) {
         // forward elimination from a zero carry; rows past the line end stay zero
         C v = zero;
         // phi two points per 16-byte load (chunk starts are 16-byte aligned)
@@ -850,14 +882,23 @@ __device__ __forceinline__ void chunked_thomas_reg(C* sa, C* cf, C* cb, const Li
                     if (t >= M - F) y[t] = cfma(Co->pb[M - 1 - t], wc, y[t]);
             }
         }
-        // psi' = 2 w - phi, two points per 16-byte access (len is even)
+        if constexpr (sizeof(C) == 16) {
 #pragma unroll
-        for (int t = 0; t < M; t += 2) {
-            if (t >= len) break;
-            float4* p4 = reinterpret_cast<float4*>(pa) + t / 2;
-            const float4 d = *p4;
-            *p4 = make_float4(fma(R(2), y[t].x, -d.x), fma(R(2), y[t].y, -d.y), fma(R(2), y[t + 1].x, -d.z),
-                              fma(R(2), y[t + 1].y, -d.w));
+            for (int t = 0; t < M; ++t) {
+                if (t >= len) break;
+                const C d = pa[t];
+                pa[t] = mkc<C>(fma(R(2), y[t].x, -d.x), fma(R(2), y[t].y, -d.y));
+            }
+        } else {
+            // psi' = 2 w - phi, two points per 16-byte access (len is even)
+#pragma unroll
+            for (int t = 0; t < M; t += 2) {
+                if (t >= len) break;
+                float4* p4 = reinterpret_cast<float4*>(pa) + t / 2;
+                const float4 d = *p4;
+                *p4 = make_float4(fma(R(2), y[t].x, -d.x), fma(R(2), y[t].y, -d.y), fma(R(2), y[t + 1].x, -d.z),
+                                  fma(R(2), y[t + 1].y, -d.w));
+            }
         }
     }
     __syncthreads();  // psi' visible to the whole CTA
@@ -1008,7 +1049,7 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
         to_sigma_y(a, b, c, ps, p, z, m);
     };
     bool paired = false;
-    if constexpr (M > 0) {
+    if constexpr (M > 0 && sizeof(C) == 8) {
         if (T.bulk) {
             // Pairs of neighbouring sites (kl even): a chunk holds an even number of
             // points and starts on a 16-byte boundary, so each component of the
@@ -1091,7 +1132,7 @@ __device__ __forceinline__ void xpass_body(const PassArgsT<C>& A, int cta, unsig
     }
     // transposed store t[mu][i][j], consecutive threads -> consecutive j
     bool pstore = false;
-    if constexpr (M > 0) {
+    if constexpr (M > 0 && sizeof(C) == 8) {
         if (((nl | ny | line0) & 1) == 0) {
             // lines j, j + 1 (j even) at the same i: one 16-byte store per channel
             pstore = true;
@@ -1152,11 +1193,22 @@ __global__ void __launch_bounds__(512) xtail_kernel(PassArgs A)
 }
 
 // With the register-resident solve of chunk length M (one-array tilings).  The
-// register caps (a few dozen bytes of spill at most) keep five to ten CTAs per SM.
-constexpr int reg_cap(int M) { return M == 16 ? 64 : (M == 24 ? 80 : 96); }
+// complex64 register caps (a few dozen bytes of spill at most) keep five to ten
+// CTAs per SM; complex128 (M = 32, 128 registers of chunk) takes 168 registers,
+// four CTAs of 96 threads, so its CTAs have at most 384 threads.
+template <typename C>
+constexpr int reg_cap(int M)
+{
+    return sizeof(C) == 16 ? 168 : (M == 16 ? 64 : (M == 24 ? 80 : 96));
+}
+template <typename C>
+constexpr int reg_threads()
+{
+    return sizeof(C) == 16 ? 384 : 512;
+}
 
 template <int MODE, typename C, int M>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) xpass_kernel_reg(PassArgsT<C> A)
+__global__ void __launch_bounds__(reg_threads<C>()) __maxnreg__(reg_cap<C>(M)) xpass_kernel_reg(PassArgsT<C> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
@@ -1242,7 +1294,7 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
         }
     };
     bool pstore = false;
-    if constexpr (M > 0) {
+    if constexpr (M > 0 && sizeof(C) == 8) {
         if (((nl | nx | line0) & 1) == 0) {
             // columns i, i + 1 (i even) at the same j: one 16-byte store per component
             pstore = true;
@@ -1325,7 +1377,7 @@ __global__ void __launch_bounds__(512) ypass_kernel(PassArgsT<C> A)
 }
 
 template <int MODE, typename C, int M>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M)) ypass_kernel_reg(PassArgsT<C> A)
+__global__ void __launch_bounds__(reg_threads<C>()) __maxnreg__(reg_cap<C>(M)) ypass_kernel_reg(PassArgsT<C> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t mbar;
@@ -1428,14 +1480,14 @@ __global__ void __launch_bounds__(512) pass_persistent(const PassArgsT<C>* args,
 
 // register-resident solve: every item's tiling is a one-array tiling of chunk length M
 template <bool X, int MODE, typename C, int M>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap<C>(M))
     pass_batched_reg(const PassArgsT<C>* args, const int2* items, const int* n_items)
 {
     batched_one<X, MODE, C, M>(args, items, n_items);
 }
 
 template <bool X, int MODE, typename C, int M>
-__global__ void __launch_bounds__(512) __maxnreg__(reg_cap(M))
+__global__ void __launch_bounds__(512) __maxnreg__(reg_cap<C>(M))
     pass_persistent_reg(const PassArgsT<C>* args, const int2* items, const int* n_items, int* work)
 {
     batched_loop<X, MODE, C, M>(args, items, n_items, work);
@@ -1513,6 +1565,11 @@ template <bool X, int MODE, typename C>
 static int launch_line_pass(const PassArgsT<C>& a, cudaStream_t st)
 {
     if (a.t.single) {
+        if constexpr (sizeof(C) == sizeof(double2)) {
+            if (a.t.m == 32)
+                return X ? launch_pass(xpass_kernel_reg<MODE, C, 32>, a, st)
+                         : launch_pass(ypass_kernel_reg<MODE, C, 32>, a, st);
+        }
         if constexpr (sizeof(C) == sizeof(float2)) {
             switch (a.t.m) {
             case 16: return X ? launch_pass(xpass_kernel_reg<MODE, C, 16>, a, st) : launch_pass(ypass_kernel_reg<MODE, C, 16>, a, st);
@@ -1521,7 +1578,8 @@ static int launch_line_pass(const PassArgsT<C>& a, cudaStream_t st)
             default: break;
             }
         }
-        return GP_ERR_ARG;  // one line array only with a register-resident solve
+        return GP_ERR_ARG;  // one line array only with a register-resident solve (complex64 m = 16/24/32,
+                            // complex128 m = 32)
     }
     return X ? launch_pass(xpass_kernel<MODE, C>, a, st) : launch_pass(ypass_kernel<MODE, C>, a, st);
 }

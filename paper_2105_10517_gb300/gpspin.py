@@ -161,7 +161,7 @@ def load():
     lib.gp_autotune.restype = ctypes.c_int
     lib.gp_tiling_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_tiling_info.restype = ctypes.c_int
-    lib.gp_set_tiling.argtypes = [vp, ip, ip, ip, ip, ip]
+    lib.gp_set_tiling.argtypes = [vp, ip, ip, ip, ip, ip, ip]
     lib.gp_plan_tiling.argtypes = [ctypes.POINTER(Params), ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_plan_tiling.restype = ctypes.c_int
     lib.gp_set_tiling.restype = ctypes.c_int
@@ -380,9 +380,11 @@ class Solver:
         _check(load().gp_autotune(self._h, int(mode), ctypes.byref(ms)), "gp_autotune")
         return ms.value
 
-    def set_tiling(self, dir, cluster=1, lines_per_cta=1, chunk=0, mode=IMAG):
-        """Force the tiling of the x-pass (dir 0) or y-pass (dir 1)."""
-        _check(load().gp_set_tiling(self._h, int(mode), int(dir), int(cluster), int(lines_per_cta), int(chunk)),
+    def set_tiling(self, dir, cluster=1, lines_per_cta=1, chunk=0, mode=IMAG, register_solve=None):
+        """Force the tiling of the x-pass (dir 0) or y-pass (dir 1); register_solve True / False
+        selects the register-resident or shared-memory solve, None the precision's default."""
+        rs = -1 if register_solve is None else int(bool(register_solve))
+        _check(load().gp_set_tiling(self._h, int(mode), int(dir), int(cluster), int(lines_per_cta), int(chunk), rs),
                "gp_set_tiling")
 
     def tiling(self, mode=IMAG):

@@ -307,3 +307,42 @@ def test_every_cluster_size(cluster, precision):
         got = s.get_state()
     tol = 1e-12 if precision == gpspin.FP64 else 4e-6
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("mode", [IMAG, REAL])
+@pytest.mark.parametrize("cluster,lines", [(1, 1), (1, 3), (2, 2), (4, 1), (8, 1)])
+def test_register_solve_complex128(cluster, lines, mode):
+    """The complex128 register-resident solve (chunk length 32 held in registers,
+    one line array in shared memory) gives the oracle's result on every cluster
+    size, with ragged last chunks shorter than the fixup length (650 = 20 x 32
+    + 10 and 610 = 19 x 32 + 2 points) and in both modes."""
+    p = ragged(nx=650, ny=610, xlen=0.05 * 650, ylen=0.05 * 610, dt=0.0005)
+    psi = smooth_plus_rough(p, 73)
+    want = oracle.propagate(p, psi, 2, mode)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        for d in (0, 1):
+            s.set_tiling(d, cluster=cluster, lines_per_cta=lines, chunk=32, mode=mode, register_solve=True)
+        t = s.tiling(mode)
+        assert t["xpass"]["register_solve"] and t["ypass"]["register_solve"]
+        assert t["xpass"]["cluster"] == cluster and t["xpass"]["chunk"] == 32
+        s.propagate(2, mode)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("mode", [IMAG, REAL])
+@pytest.mark.parametrize("which", ["X", "Y"])
+def test_register_solve_complex128_substeps(which, mode):
+    """Single X and Y substeps with the complex128 register-resident solve on the
+    72 x 45 grid (chunks of 32, 32, 8 and 32, 13 points)."""
+    p = ragged()
+    psi = smooth_plus_rough(p, 5)
+    want = oracle.substep(p, psi, which, mode)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        for d in (0, 1):
+            s.set_tiling(d, cluster=1, lines_per_cta=2, chunk=32, mode=mode, register_solve=True)
+        s.apply_substep(which, mode)
+        got = s.get_state()
+    assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
