@@ -74,12 +74,12 @@ BYTES_PER_SITE_PASS = 96
 # one ncu capture of that kernel), keyed by kernel and workload and valid only
 # while the kernel source is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
-    "xpass_kernel<1, double2> quench1024": (59190528 + 5368576, "cfb31e554006dbf4"),
-    "ypass_kernel<1, double2> quench1024": (58736384 + 6190848, "cfb31e554006dbf4"),
-    "xpass_kernel<0, double2> vortex512": (16203008 + 768, "cfb31e554006dbf4"),
-    "ypass_kernel<0, double2> vortex512": (16174336 + 256, "cfb31e554006dbf4"),
-    "xpass_kernel_reg<0, float2, 32> precision2048": (105458432 + 55552000, "cfb31e554006dbf4"),
-    "ypass_kernel_reg<0, float2, 32> precision2048": (105446144 + 56904704, "cfb31e554006dbf4"),
+    "xpass_kernel<1, double2> quench1024": (57513728 + 9970688, "9cd44b01d8d15a4c"),
+    "ypass_kernel_reg<1, double2, 32> quench1024": (57548800 + 6869760, "9cd44b01d8d15a4c"),
+    "xpass_kernel<0, double2> vortex512": (16203264 + 0, "9cd44b01d8d15a4c"),
+    "ypass_kernel<0, double2> vortex512": (16172288 + 0, "9cd44b01d8d15a4c"),
+    "xpass_kernel_reg<0, float2, 32> precision2048": (105457664 + 56003072, "9cd44b01d8d15a4c"),
+    "ypass_kernel_reg<0, float2, 32> precision2048": (105457920 + 57491456, "9cd44b01d8d15a4c"),
 }
 
 L2_FLUSH_BYTES = 256 << 20
