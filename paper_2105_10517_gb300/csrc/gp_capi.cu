@@ -885,12 +885,26 @@ int gp_propagate_host(gp_handle* h, const double* psi_in, long long nsteps, int 
     ax.t.bulk = 0;
     if (mode == GP_IMAG) ay.partials = h->partials;
     ay.mcomp = mc;
+    // In real time nothing is pending after a step: the last y-pass stores the
+    // result into the caller's buffer beside the handle's state, so no copy
+    // follows the step (the writes travel to the host during the pass).
+    const bool direct = dout && mode == GP_REAL;
+    if (direct && nsteps == 1) ay.out_host = dout;
     if ((st = enqueue_steps(h, mode, ax, ay, gy, 1))) return st;
     if (mode == GP_IMAG && !mc) h->scale_pending = true;
     h->steps += 1;
-    if (nsteps > 1 && (st = propagate_active(h, nsteps - 1, mode))) return st;
+    if (direct && nsteps > 1) {
+        if (nsteps > 2 && (st = propagate_active(h, nsteps - 2, mode))) return st;
+        PassArgs bx = pass_args(h, cs, 0), by = pass_args(h, cs, 1);
+        by.out_host = dout;
+        if ((st = enqueue_steps(h, mode, bx, by, gy, 1))) return st;
+        h->steps += 1;
+    } else if (nsteps > 1 && (st = propagate_active(h, nsteps - 1, mode))) {
+        return st;
+    }
     if ((st = check_flags(h))) return st;
     if (!dout) return gp_get_state(h, psi_out);
+    if (direct) return GP_OK;  // check_flags synchronised the stream: the result is in place
     // the normalised result is written straight into the caller's buffer
     LK(launch_scaled_copy(dout, h->psi, n_elems(h), h->scal, h->stream));
     return sync_status(h);

@@ -50,6 +50,24 @@ def test_matches_the_three_calls(mode, buffers):
         assert np.array_equal(s.get_state(), want)  # the handle holds the new state
 
 
+@pytest.mark.parametrize("n", [1, 2, 3])
+@pytest.mark.parametrize("in_place", [False, True])
+def test_real_time_result_written_by_the_last_pass(n, in_place):
+    """In real time the last y-pass stores the result into the caller's pinned
+    buffer beside the handle's state (no copy after the step): bitwise the
+    three-call result for one, two and three steps, also in place."""
+    p = params(so_type=2, rabi=0.5)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=23, phase_noise=0.1)
+    want = reference(p, psi, n, gpspin.REAL)
+    hin = torch.from_numpy(psi.copy()).pin_memory()
+    hout = hin if in_place else torch.empty_like(hin).pin_memory()
+    with gpspin.Solver(p) as s:
+        s.propagate_host(hin, n, gpspin.REAL, out=hout)
+        assert np.array_equal(hout.numpy(), want)
+        assert np.array_equal(s.get_state(), want)
+        assert s.observables()["steps"] == n
+
+
 def test_in_place_and_zero_steps():
     p = params(so_type=2, omeg=-0.4)
     psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=5, phase_noise=0.1)
