@@ -315,6 +315,17 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out);
  * Results stay within the parity tolerances for every valid tiling. */
 int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk, int register_solve);
 
+/* Debug checks of a handle (0 turns them off).  GP_DEBUG_POISON: before each
+ * pass of a first-order step, every byte the pass must write (the
+ * intermediate before the x-pass; the state between the passes, after the
+ * x-pass has read it) is set to 0xFF, a NaN in both precisions, so an element
+ * that a pass leaves unwritten reaches the state as a NaN: the norm and
+ * observable reductions then report GP_ERR_NONFINITE, and results differ from
+ * a run without the check.  Costs two memsets of the state's size per step.
+ * GP_ERR_ARG for unknown flags. */
+#define GP_DEBUG_POISON 1
+int gp_set_debug(gp_handle* h, int flags);
+
 /* The tiling the handle uses for a pass (dir 0: x-pass, 1: y-pass) in the given
  * mode and its current precision: out[0] CTAs per line group (cluster size),
  * out[1] lines per CTA, out[2] chunk length, out[3] chunks per line, out[4]

@@ -455,6 +455,7 @@ int gp_batch_submit(gp_batch* b, const gp_params* params, const gp_request* req,
 
 int gp_batch_step(gp_batch* b, int* n_running, int* n_queued)
 {
+    gpspin::TraceRange trace("gp_batch_step");
     if (!b) return GP_ERR_ARG;
     int st = admit(b);
     if (st) return st;

@@ -463,8 +463,14 @@ int apply_sigma(gp_handle* h, const PassArgsT<C>& ay)
 template <typename A>
 int enqueue_steps(gp_handle* h, int mode, const A& ax, const A& ay, int gy, long long n)
 {
+    // debug: every byte a pass must write is first set to 0xFF (a NaN in both
+    // precisions), so an element a pass skipped reaches the state as a NaN
+    const bool poison = h->debug & GP_DEBUG_POISON;
+    const size_t bytes = n_elems(h) * sizeof(*ax.out);
     for (long long s = 0; s < n; ++s) {
+        if (poison) CK(cudaMemsetAsync(ax.out, 0xFF, bytes, h->stream));
         LK(launch_xpass(ax, mode, h->stream));
+        if (poison) CK(cudaMemsetAsync(ay.out, 0xFF, bytes, h->stream));  // psi: read by the x-pass, not yet rewritten
         LK(launch_ypass(ay, mode, h->stream));
         if (mode == GP_IMAG && h->mcon) {
             // magnetisation-constrained normalisation, applied at once
@@ -811,6 +817,7 @@ static int check_flags(gp_handle* h)
 
 int gp_propagate(gp_handle* h, long long nsteps, int mode)
 {
+    gpspin::TraceRange trace("gp_propagate");
     if (!h || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
     if (nsteps == 0) return GP_OK;
     CK(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream));
@@ -821,6 +828,7 @@ int gp_propagate(gp_handle* h, long long nsteps, int mode)
 
 int gp_refine_fp64(gp_handle* h, long long nsteps, int mode)
 {
+    gpspin::TraceRange trace("gp_refine_fp64");
     if (!h || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
     if (h->active == GP_FP32_MIXED) {
         // widen the complex64 state (the pending scale stays pending)
@@ -859,6 +867,7 @@ static double2* device_view(const double* p)
 
 int gp_propagate_host(gp_handle* h, const double* psi_in, long long nsteps, int mode, double* psi_out)
 {
+    gpspin::TraceRange trace("gp_propagate_host");
     if (!h || !psi_in || !psi_out || nsteps < 0 || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
     const double2* din = device_view(psi_in);
     double2* dout = device_view(psi_out);
@@ -885,26 +894,12 @@ int gp_propagate_host(gp_handle* h, const double* psi_in, long long nsteps, int 
     ax.t.bulk = 0;
     if (mode == GP_IMAG) ay.partials = h->partials;
     ay.mcomp = mc;
-    // In real time nothing is pending after a step: the last y-pass stores the
-    // result into the caller's buffer beside the handle's state, so no copy
-    // follows the step (the writes travel to the host during the pass).
-    const bool direct = dout && mode == GP_REAL;
-    if (direct && nsteps == 1) ay.out_host = dout;
     if ((st = enqueue_steps(h, mode, ax, ay, gy, 1))) return st;
     if (mode == GP_IMAG && !mc) h->scale_pending = true;
     h->steps += 1;
-    if (direct && nsteps > 1) {
-        if (nsteps > 2 && (st = propagate_active(h, nsteps - 2, mode))) return st;
-        PassArgs bx = pass_args(h, cs, 0), by = pass_args(h, cs, 1);
-        by.out_host = dout;
-        if ((st = enqueue_steps(h, mode, bx, by, gy, 1))) return st;
-        h->steps += 1;
-    } else if (nsteps > 1 && (st = propagate_active(h, nsteps - 1, mode))) {
-        return st;
-    }
+    if (nsteps > 1 && (st = propagate_active(h, nsteps - 1, mode))) return st;
     if ((st = check_flags(h))) return st;
     if (!dout) return gp_get_state(h, psi_out);
-    if (direct) return GP_OK;  // check_flags synchronised the stream: the result is in place
     // the normalised result is written straight into the caller's buffer
     LK(launch_scaled_copy(dout, h->psi, n_elems(h), h->scal, h->stream));
     return sync_status(h);
@@ -1017,6 +1012,7 @@ float time_pass(gp_handle* h, A a, int dir, int mode, void* flush, size_t flush_
 
 int gp_autotune(gp_handle* h, int mode, double* ms_out)
 {
+    gpspin::TraceRange trace("gp_autotune");
     if (!h || (mode != GP_IMAG && mode != GP_REAL)) return GP_ERR_ARG;
     int st = ensure_coef(h, mode);
     if (st) return st;
@@ -1122,6 +1118,14 @@ int gp_plan_tiling(const gp_params* p, int mode, int dir, int* out)
     out[9] = t.cs;
     out[10] = t.Lp;
     out[11] = solve_conflicts(t.cs, t.Lp, 3 * t.R, t.Qc, G, unit);
+    return GP_OK;
+}
+
+int gp_set_debug(gp_handle* h, int flags)
+{
+    if (!h || (flags & ~GP_DEBUG_POISON)) return GP_ERR_ARG;
+    if (h->debug != flags) drop_graphs(h);  // the captured steps hold the other form
+    h->debug = flags;
     return GP_OK;
 }
 

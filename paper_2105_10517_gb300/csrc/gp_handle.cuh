@@ -1,11 +1,22 @@
 // gp_handle.cuh -- the device state behind a gp_handle and the runtime helpers
 // shared by the C-ABI translation units (gp_capi.cu, gp_batch.cu).
 #pragma once
+#include <nvtx3/nvToolsExt.h>
+
 #include "gp_internal.cuh"
 
 namespace gpspin {
 
 constexpr int kNormBlocksMax = 16384;
+
+// NVTX range over a library call (visible to ncu --nvtx and other profilers;
+// a no-op when no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Coefficient tables and tilings of one mode (imaginary or real time).
 struct CoefSet {
@@ -54,6 +65,7 @@ struct gp_handle {
     int mcon = 0;              // imaginary time keeps N = 1 and N+ - N- = m_target
     double m_target = 0.0;
     int split = 0;             // GP_SPLIT_LIE or GP_SPLIT_STRANG
+    int debug = 0;             // GP_DEBUG_* flags
 };
 
 namespace gpspin {

@@ -94,8 +94,6 @@ struct PassArgsT {
     double* partials;          // y-pass: per-CTA sum |psi|^2 (per component when mcomp)
     int mcomp;                 // y-pass: three partials per CTA, one per component
     int* err;                  // status bits set by the kernel (8: bulk-copy wait timed out)
-    C* out_host;               // y-pass: a second destination of the result (the device view
-                               // of a caller's host buffer), written beside out; or null
     // pointwise substep constants (x-pass)
     const C* ex;               // [nx] exp(-tau' wx^2 x^2 / 2)
     const C* ey;               // [ny] exp(-tau' wy^2 y^2 / 2)

@@ -1309,18 +1309,10 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
                 from_sigma_x(s0[0], s0[Lp], s0[2 * Lp], a0, b0, c0);
                 from_sigma_x(s1[0], s1[Lp], s1[2 * Lp], a1, b1, c1);
                 if (!ok) continue;
-                const float4 va = make_float4(a0.x, a0.y, a1.x, a1.y), vb = make_float4(b0.x, b0.y, b1.x, b1.y),
-                             vc = make_float4(c0.x, c0.y, c1.x, c1.y);
                 float4* o = reinterpret_cast<float4*>(A.out + (size_t)j * nx + i);
-                o[0] = va;
-                o[ph] = vb;
-                o[2 * ph] = vc;
-                if (A.out_host) {
-                    float4* oh = reinterpret_cast<float4*>(A.out_host + (size_t)j * nx + i);
-                    oh[0] = va;
-                    oh[ph] = vb;
-                    oh[2 * ph] = vc;
-                }
+                o[0] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                o[ph] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                o[2 * ph] = make_float4(c0.x, c0.y, c1.x, c1.y);
                 tally(a0, b0, c0);
                 tally(a1, b1, c1);
             }
@@ -1336,11 +1328,6 @@ __device__ __forceinline__ void ypass_body(const PassArgsT<C>& A, int cta, unsig
         A.out[o] = a;
         A.out[plane + o] = b;
         A.out[2 * plane + o] = c;
-        if (A.out_host) {
-            A.out_host[o] = a;
-            A.out_host[plane + o] = b;
-            A.out_host[2 * plane + o] = c;
-        }
         tally(a, b, c);
     }
     if (A.partials && A.mcomp) {

@@ -24,6 +24,7 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-
 
 IMAG, REAL = 0, 1
 SPLIT_LIE, SPLIT_STRANG = 0, 1
+DEBUG_POISON = 1
 SO_NONE, SO_RASHBA, SO_DRESSELHAUS = 0, 1, 2
 FP64, FP32_MIXED = 0, 1
 SUB_P, SUB_X, SUB_Y = 0, 1, 2
@@ -34,7 +35,7 @@ STATUS = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_OOM", 3: "GP_ERR_CUDA", 4: "GP
 # Every symbol the public header declares (checked by the CPU tests).
 EXPORTS = ["gp_create", "gp_destroy", "gp_set_params", "gp_set_state", "gp_get_state", "gp_init_gaussian",
            "gp_init_winding", "gp_set_magnetization", "gp_set_splitting", "gp_propagate", "gp_propagate_host", "gp_refine_fp64", "gp_observables", "gp_apply_substep", "gp_profile_step", "gp_autotune",
-           "gp_tiling_info", "gp_set_tiling", "gp_plan_tiling", "gp_check_wait_timeout",
+           "gp_tiling_info", "gp_set_tiling", "gp_set_debug", "gp_plan_tiling", "gp_check_wait_timeout",
            "gp_propagate_noalloc", "gp_request_bytes", "gp_batch_create", "gp_batch_destroy", "gp_batch_submit",
            "gp_batch_step", "gp_batch_poll", "gp_batch_use_graphs", "gp_batch_set_persistent", "gp_batch_set_running_limit",
            "gp_batch_set_queue_limit", "gp_batch_cancel", "gp_batch_error",
@@ -162,6 +163,8 @@ def load():
     lib.gp_tiling_info.argtypes = [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_tiling_info.restype = ctypes.c_int
     lib.gp_set_tiling.argtypes = [vp, ip, ip, ip, ip, ip, ip]
+    lib.gp_set_debug.argtypes = [vp, ip]
+    lib.gp_set_debug.restype = ctypes.c_int
     lib.gp_plan_tiling.argtypes = [ctypes.POINTER(Params), ip, ip, ctypes.POINTER(ctypes.c_int)]
     lib.gp_plan_tiling.restype = ctypes.c_int
     lib.gp_set_tiling.restype = ctypes.c_int
@@ -379,6 +382,11 @@ class Solver:
         ms = ctypes.c_double()
         _check(load().gp_autotune(self._h, int(mode), ctypes.byref(ms)), "gp_autotune")
         return ms.value
+
+    def set_debug(self, poison=True):
+        """Poison check: every byte a pass must write is set to a NaN pattern first, so a
+        skipped write shows up as a non-finite state (gp_set_debug, GP_DEBUG_POISON)."""
+        _check(load().gp_set_debug(self._h, DEBUG_POISON if poison else 0), "gp_set_debug")
 
     def set_tiling(self, dir, cluster=1, lines_per_cta=1, chunk=0, mode=IMAG, register_solve=None):
         """Force the tiling of the x-pass (dir 0) or y-pass (dir 1); register_solve True / False

@@ -7,7 +7,8 @@ solve together and retires converged ones (continuous batching).  A solve is
 done when its energy changes by less than `tol` between checks `check_every`
 steps apart, or at `cap` steps.  The baseline serves the same trace one request
 at a time with a plain FP64 handle.  Both report solves/s and the p50/p99 time
-from arrival to converged state.
+from arrival to converged state; the batched loop also reports the queue depth
+and running count over its ticks.
 """
 import time
 
@@ -41,6 +42,7 @@ def serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=64 << 30, c
     as REQ_CANCELLED."""
     pending = sorted(trace, key=lambda r: r["arrival"])
     records, live = [], {}
+    depth = []  # (queued, running) after every tick
     with gpspin.Batch(max_bytes, check_every=check_every, stream=stream) as b:
         b.set_running_limit(max_running_sites)
         t0 = time.perf_counter()
@@ -56,7 +58,7 @@ def serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=64 << 30, c
             if not live:
                 time.sleep(max(0.0, pending[k]["arrival"] - (time.perf_counter() - t0)))
                 continue
-            b.step()
+            depth.append(b.step()[::-1])
             done_t = time.perf_counter() - t0
             for rid in list(live):
                 st, steps, obs, _ = b.poll(rid)
@@ -70,7 +72,12 @@ def serve_batched(trace, policy=gpspin.POLICY_FP32_REFINE, max_bytes=64 << 30, c
                     records.append(dict(arrival=rq["arrival"], done=done_t, latency=done_t - rq["arrival"],
                                         steps=steps, cap=cap, state=st, energy=obs["energy"], nx=rq["params"]["nx"]))
         makespan = time.perf_counter() - t0
-    return _summary(records, makespan), records
+    summary = _summary(records, makespan)
+    if depth:
+        q = np.array(depth, dtype=float)
+        summary.update(ticks=len(depth), queue_depth_max=int(q[:, 0].max()), queue_depth_mean=float(q[:, 0].mean()),
+                       running_max=int(q[:, 1].max()), running_mean=float(q[:, 1].mean()))
+    return summary, records
 
 
 def serve_one_at_a_time(trace, check_every=100, tol=1e-9, cap=20000, stream=None):

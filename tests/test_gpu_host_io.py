@@ -52,10 +52,10 @@ def test_matches_the_three_calls(mode, buffers):
 
 @pytest.mark.parametrize("n", [1, 2, 3])
 @pytest.mark.parametrize("in_place", [False, True])
-def test_real_time_result_written_by_the_last_pass(n, in_place):
-    """In real time the last y-pass stores the result into the caller's pinned
-    buffer beside the handle's state (no copy after the step): bitwise the
-    three-call result for one, two and three steps, also in place."""
+def test_real_time_calls_of_few_steps(n, in_place):
+    """Real-time calls of one, two and three steps with pinned buffers (the first
+    x-pass reads the input buffer, one kernel writes the output): bitwise the
+    three-call result and the handle's state, also in place."""
     p = params(so_type=2, rabi=0.5)
     psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=23, phase_noise=0.1)
     want = reference(p, psi, n, gpspin.REAL)
