@@ -169,7 +169,7 @@ struct gp_batch {
     Group<float2> g32;
     int* counts = nullptr;  // device: kGroupCounts per precision group (complex128, complex64)
     int* work = nullptr;    // device: the persistent launches' item counters, two ints per group
-    // batched launch form: < 0 one CTA per item (the default: measured 0-2% faster
+    // batched launch form: < 0 one CTA per item (the default: measured 1-6% faster
     // than the persistent form on the serving mix); 0 persistent, one CTA per
     // resident slot; > 0 persistent with at most that many CTAs
     int persist = -1;

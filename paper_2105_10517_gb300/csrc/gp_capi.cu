@@ -1145,7 +1145,6 @@ int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_ct
                      lines_per_cta, chunk, &t);
     if (st) return st;
     if (register_solve == 1 && !t.single) return GP_ERR_UNSUPPORTED;  // chunk longer than the compiled ones
-    if (st) return st;
     (f32 ? (dir == 0 ? cs.ftx : cs.fty) : (dir == 0 ? cs.tx : cs.ty)) = t;
     drop_graphs(h);
     return GP_OK;

@@ -67,3 +67,14 @@ def test_noalloc_rejects_before_any_device_work(lib):
     big = gpspin.make_params(dict(nx=257, ny=16, xlen=8.0, ylen=8.0, dt=0.01))
     assert lib.gp_propagate_noalloc(ctypes.byref(big), ctypes.c_void_p(0x1000), 1, 0, None) == 6
     assert lib.gp_propagate_noalloc(ctypes.byref(p), None, 1, 0, None) == 1
+
+
+def test_null_handles_are_rejected_without_a_device(lib):
+    """The entry points added for the solve kind, the debug checks and the batched
+    launch form check their arguments on the host first (GP_ERR_ARG = 1)."""
+    lib = gpspin.load()
+    assert lib.gp_set_debug(None, gpspin.DEBUG_POISON) == 1
+    assert lib.gp_set_tiling(None, 0, 0, 1, 1, 32, 1) == 1
+    assert lib.gp_batch_set_persistent(None, 0) == 1
+    assert lib.gp_batch_use_graphs(None, 1) == 1
+
