@@ -77,3 +77,25 @@ def test_full_size_1024_autotuned(mode):
         e = s.observables()["energy"]
     assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
     assert abs(e - oracle.observables(p, want)["energy"]) <= 1e-12 * abs(e)
+
+
+@pytest.mark.parametrize("name", ["imag256", "real256"])
+def test_thousand_step_parity_register_solve(name):
+    """The 1000-step contract with the register-resident complex128 solve in both
+    passes (the solve the autotuner picks for the 1024^2 y-pass), over 2-CTA
+    clusters: the chunk carries cross distributed shared memory every step."""
+    p, mode = case(name)
+    psi = inputs.gaussian_state(p["nx"], p["ny"], p["xlen"], p["ylen"], seed=19)
+    want = oracle.propagate(p, psi, 1000, mode)
+    with gpspin.Solver(p) as s:
+        s.set_state(psi)
+        for d in (0, 1):
+            s.set_tiling(d, cluster=2, lines_per_cta=2, chunk=32, mode=mode, register_solve=True)
+        t = s.tiling(mode)
+        assert t["xpass"]["register_solve"] and t["ypass"]["register_solve"] and t["ypass"]["cluster"] == 2
+        s.propagate(1000, mode)
+        got = s.get_state()
+        obs = s.observables()
+    o = oracle.observables(p, want)
+    assert np.max(np.abs(got - want)) <= 1e-10
+    assert abs(obs["energy"] - o["energy"]) <= 1e-12 * abs(o["energy"])
