@@ -316,7 +316,9 @@ int gp_autotune(gp_handle* h, int mode, double* ms_out);
 int gp_set_tiling(gp_handle* h, int mode, int dir, int cluster, int lines_per_cta, int chunk, int register_solve);
 
 /* Debug checks of a handle (0 turns them off).  GP_DEBUG_POISON: before each
- * pass of a first-order step, every byte the pass must write (the
+ * pass of the first-order steps that gp_propagate, gp_refine_fp64 and
+ * gp_propagate_host run (not the batched, second-order, single-substep or
+ * no-allocation paths), every byte the pass must write (the
  * intermediate before the x-pass; the state between the passes, after the
  * x-pass has read it) is set to 0xFF, a NaN in both precisions, so an element
  * that a pass leaves unwritten reaches the state as a NaN: the norm and
