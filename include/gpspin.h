@@ -293,8 +293,8 @@ int gp_batch_poll(gp_batch* b, long long id, int* state, long long* steps, gp_ob
  * one CTA or a cluster of 2, 4 or 8 CTAs per line group, chunk lengths of the
  * parallel Thomas solve, and for complex128 the shared-memory and the
  * register-resident solve -- on the handle's stream, and keeps the fastest for
- * later propagation.  Each candidate is timed as the best of three launches,
- * each started from a cold L2 (a scratch buffer of 1.5 x the L2 size is
+ * later propagation.  Each candidate is timed as the median of five launches
+ * (after one warm-up), each started from a cold L2 (a scratch buffer of 1.5 x the L2 size is
  * written first; from a warm L2 if that buffer cannot be allocated).  The
  * state is saved and restored, so tuning does not change the solve; results
  * stay within the parity tolerances (only the summation order of partial

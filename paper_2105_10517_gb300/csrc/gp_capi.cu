@@ -11,6 +11,7 @@
 #include "../../include/gpspin.h"
 #include "gp_internal.cuh"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <complex>
@@ -986,16 +987,19 @@ int gp_profile_step(gp_handle* h, int mode, float* ms_out)
 }
 
 extern "C++" {
-// Times one pass (x: dir 0, y: dir 1) with the given tiling: best of three
-// launches on the handle's stream, in ms (negative if the launch fails).  With
-// a flush buffer each timed launch starts from a cold L2 (the buffer, larger
-// than L2, is written first), as in a step whose input has left the cache.
+// Times one pass (x: dir 0, y: dir 1) with the given tiling: the median of five
+// launches after one warm-up, on the handle's stream, in ms (negative if a
+// launch fails).  The median, not the minimum: candidates within a few percent
+// of each other would otherwise be ranked by their luckiest launch.  With a
+// flush buffer each timed launch starts from a cold L2 (the buffer, larger than
+// L2, is written first), as in a step whose input has left the cache.
 template <typename A>
 float time_pass(gp_handle* h, A a, int dir, int mode, void* flush, size_t flush_bytes)
 {
     a.partials = nullptr;
-    float best = -1.0f;
-    for (int rep = 0; rep < 4; ++rep) {
+    constexpr int kTimed = 5;
+    float t[kTimed];
+    for (int rep = 0; rep <= kTimed; ++rep) {
         if (flush && cudaMemsetAsync(flush, rep, flush_bytes, h->stream) != cudaSuccess) return -1.0f;
         if (cudaEventRecord(h->ev[0], h->stream) != cudaSuccess) return -1.0f;
         int rc = dir == 0 ? launch_xpass(a, mode, h->stream) : launch_ypass(a, mode, h->stream);
@@ -1003,9 +1007,10 @@ float time_pass(gp_handle* h, A a, int dir, int mode, void* flush, size_t flush_
             return -1.0f;
         float ms = 0;
         cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
-        if (rep > 0 && (best < 0 || ms < best)) best = ms;  // the first launch warms up
+        if (rep > 0) t[rep - 1] = ms;  // the first launch warms up
     }
-    return best;
+    std::sort(t, t + kTimed);
+    return t[kTimed / 2];
 }
 
 }  // extern "C++"
